@@ -1,0 +1,993 @@
+/*
+ * aeqc_oracle.c -- plain, slow, FP64 CPU oracle for the hybrid compressor's
+ * hot path (autoencoder -> error-bounded residual quantizer -> QoI-preserving
+ * Lagrange/Newton correction) of Banerjee et al., "Scalable Hybrid Learning
+ * Techniques for Scientific Data Compression" (arXiv:2212.10733).
+ *
+ * THIS FILE IS TEST INFRASTRUCTURE.  Only the test suite, the smoke check and
+ * the benchmark's CPU-baseline leg may load it.  It shares no code, header,
+ * table or constant generator with the CUDA library; the two only meet on the
+ * same input bytes.
+ *
+ * Style: plain loops, FP64, fixed summation order, no blocking, no fusion, no
+ * separability shortcuts.  Build with -O2 -fno-fast-math -ffp-contract=off so
+ * no multiply-add is contracted behind the reader's back.
+ *
+ * Paper passages followed (section / equation of the paper):
+ *   - QoI definitions n, u_par, T_perp, T_par ......... Sec. II, Eq. (1)-(4)
+ *   - AE loss MSE(X, Xhat) ............................. Sec. III Stage 2, Eq. (5)
+ *   - AE shape: tied dense layers, linear activation,
+ *     Adam lr 1e-3, batch 128, Z-score normalisation ... Sec. IV-B/C
+ *   - residual processing with an error-bounded
+ *     compressor, selective per image ................. Sec. III Stage 4
+ *   - dual maximisation by Newton with step s,
+ *     s = 1, at most 50 iterations ..................... Sec. III Stage 5, Eq. (6)
+ *   - four multipliers per mesh node, correction
+ *     applied to every value on decompression ......... Sec. III Stage 5
+ *   - non-converged images: second round with a small
+ *     step and 400 iterations, then stored verbatim ... Sec. IV-E (parameter study)
+ *   - NRMSE .............................................. Sec. IV-A, Eq. (7)
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - loss of the correction: generalised KL (I-divergence)
+ *     sum vol (f log(f/x') - f + x'), whose stationarity gives
+ *     f = x' exp(-lambda . phi); an L2 variant (f = x' - lambda . phi) is kept
+ *     for the closed-form checks;
+ *   - phi = (1, v_par, v_perp^2, v_par^2): preserving these four linear
+ *     moments preserves n, u_par, T_perp and T_par (Eq. (1)-(4));
+ *   - residual quantizer: uniform, power-of-two bin Delta = 2^floor(log2(2 alpha e)),
+ *     e = tau * max(x), round-half-even of the exact difference, codes int16;
+ *     one extra reconstruction level at exactly 0 (code -32767), taken when it
+ *     is strictly nearer to x than xhat + q Delta (removes the positive bias a
+ *     clamp at zero would put on every near-empty cell); escape code -32768
+ *     stores the raw value;
+ *   - convergence: max_k |g_k| / S_k <= tol with S_k = sum vol |phi_k| f,
+ *     tested before each step;
+ *   - round 2: damped Newton from zero with backtracking (a fixed s = 0.01
+ *     cannot reach 1e-12 in 400 steps);
+ *   - end-to-end check |f - x| <= e for every point; one retry with alpha/4,
+ *     else verbatim; a histogram neither Newton round solves is verbatim.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------- */
+/* Types (mirrored by hand in the Python wrapper; never included elsewhere)  */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+  int n_par;            /* number of v_par nodes, index i (fastest) */
+  int n_perp;           /* number of v_perp nodes, index j */
+  const double* vpar;   /* [n_par] */
+  const double* vperp;  /* [n_perp] */
+  const double* vol;    /* [n_perp * n_par] cell volumes, or NULL */
+  double vol_uniform;   /* used when vol == NULL */
+  double mass;          /* particle mass m; scales T only */
+} or_grid;
+
+typedef struct {
+  double tau;           /* pointwise bound e = tau * max(x) */
+  double alpha;         /* share of e given to the quantizer */
+  double step_s;        /* Newton step size s of Eq. (6) */
+  double tol;           /* convergence: max_k |g_k|/S_k <= tol */
+  int max_iter;         /* round-1 iteration cap (50) */
+  int r2_max_iter;      /* round-2 iteration cap (400) */
+  int loss;             /* 0: generalised KL (exponential), 1: L2 */
+  int warm_iters;       /* warm-start probation iterations (2) */
+  double warm_reject;   /* reject warm start if residual above this (1e-8) */
+  double qoi_check;     /* end-to-end moment check (1e-10) */
+} or_params;
+
+/* per-histogram status bits */
+#define ST_CONVERGED 0x0001u
+#define ST_ROUND2 0x0002u
+#define ST_VERBATIM 0x0004u
+#define ST_NONFINITE_INPUT 0x0008u
+#define ST_ZERO_IMAGE 0x0010u
+#define ST_CODE_ESCAPE 0x0020u
+#define ST_WARM_REJECTED 0x0040u
+#define ST_ALPHA_RETRY 0x0080u
+#define ST_AE_EXACT 0x0100u
+
+#define CODE_ESCAPE (-32768)
+#define CODE_ZERO (-32767)
+#define CODE_MAX 32766
+
+static double vol_at(const or_grid* g, int j, int i) {
+  return g->vol ? g->vol[(size_t)j * g->n_par + i] : g->vol_uniform;
+}
+
+/* phi_k at node (j, i): 1, v_par, v_perp^2, v_par^2. */
+static double phi_at(const or_grid* g, int k, int j, int i) {
+  double vp = g->vpar[i], vq = g->vperp[j];
+  switch (k) {
+    case 0: return 1.0;
+    case 1: return vp;
+    case 2: return vq * vq;
+    default: return vp * vp;
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. (1)-(4): the four linear moments and the QoIs derived from them        */
+/* ------------------------------------------------------------------------- */
+
+/* Q_k = sum_j sum_i vol_ij phi_k(i,j) x_ij, row j outer, column i inner.
+ * The same routine evaluates the Newton residual so that x' = x gives g = 0
+ * bit for bit. */
+static void moments_one(const or_grid* g, const double* x, double Q[4]) {
+  double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
+  for (int j = 0; j < g->n_perp; ++j) {
+    for (int i = 0; i < g->n_par; ++i) {
+      double w = vol_at(g, j, i) * x[(size_t)j * g->n_par + i];
+      q0 += w * phi_at(g, 0, j, i);
+      q1 += w * phi_at(g, 1, j, i);
+      q2 += w * phi_at(g, 2, j, i);
+      q3 += w * phi_at(g, 3, j, i);
+    }
+  }
+  Q[0] = q0; Q[1] = q1; Q[2] = q2; Q[3] = q3;
+}
+
+/* Absolute-moment scales S_k = sum vol |phi_k| x (normalise residuals). */
+static void abs_moments_one(const or_grid* g, const double* x, double S[4]) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (int j = 0; j < g->n_perp; ++j) {
+    for (int i = 0; i < g->n_par; ++i) {
+      double w = vol_at(g, j, i) * fabs(x[(size_t)j * g->n_par + i]);
+      s0 += w * fabs(phi_at(g, 0, j, i));
+      s1 += w * fabs(phi_at(g, 1, j, i));
+      s2 += w * fabs(phi_at(g, 2, j, i));
+      s3 += w * fabs(phi_at(g, 3, j, i));
+    }
+  }
+  S[0] = s0; S[1] = s1; S[2] = s2; S[3] = s3;
+}
+
+void or_moments(const or_grid* g, const double* x, int64_t n, double* Q) {
+  const size_t P = (size_t)g->n_par * g->n_perp;
+#pragma omp parallel for schedule(static)
+  for (int64_t b = 0; b < n; ++b) moments_one(g, x + (size_t)b * P, Q + 4 * b);
+}
+
+void or_abs_moments(const or_grid* g, const double* x, int64_t n, double* S) {
+  const size_t P = (size_t)g->n_par * g->n_perp;
+#pragma omp parallel for schedule(static)
+  for (int64_t b = 0; b < n; ++b) abs_moments_one(g, x + (size_t)b * P, S + 4 * b);
+}
+
+/* QoIs from the moments: n = Q0, u = Q1/Q0, T_perp = m Q2 / (2 Q0),
+ * T_par = m (Q3/Q0 - u^2) / 2 (Eq. (4) with (v - u)^2 expanded). */
+void or_qois_from_moments(const double* Q, int64_t n, double mass, double* out) {
+  for (int64_t b = 0; b < n; ++b) {
+    const double* q = Q + 4 * b;
+    double dens = q[0], u = q[1] / q[0];
+    out[4 * b + 0] = dens;
+    out[4 * b + 1] = u;
+    out[4 * b + 2] = 0.5 * mass * q[2] / q[0];
+    out[4 * b + 3] = 0.5 * mass * (q[3] / q[0] - u * u);
+  }
+}
+
+/* QoIs straight from the integrals of Eq. (1)-(4), T_par with (v_par - u)^2
+ * inside the integral.  Used only to check the identity above. */
+void or_qois_direct(const or_grid* g, const double* x, int64_t n, double* out) {
+  const size_t P = (size_t)g->n_par * g->n_perp;
+  for (int64_t b = 0; b < n; ++b) {
+    const double* xb = x + (size_t)b * P;
+    double dens = 0.0, flow = 0.0;
+    for (int j = 0; j < g->n_perp; ++j)
+      for (int i = 0; i < g->n_par; ++i) {
+        double w = vol_at(g, j, i) * xb[(size_t)j * g->n_par + i];
+        dens += w;
+        flow += w * g->vpar[i];
+      }
+    double u = flow / dens;
+    double tperp = 0.0, tpar = 0.0;
+    for (int j = 0; j < g->n_perp; ++j)
+      for (int i = 0; i < g->n_par; ++i) {
+        double w = vol_at(g, j, i) * xb[(size_t)j * g->n_par + i];
+        double dv = g->vpar[i] - u;
+        tperp += w * g->mass * g->vperp[j] * g->vperp[j];
+        tpar += w * g->mass * dv * dv;
+      }
+    out[4 * b + 0] = dens;
+    out[4 * b + 1] = u;
+    out[4 * b + 2] = 0.5 * tperp / dens;
+    out[4 * b + 3] = 0.5 * tpar / dens;
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Stage 4: error-bounded residual quantizer                                  */
+/* ------------------------------------------------------------------------- */
+
+/* Bin width Delta = 2^floor(log2(2 alpha e)) for a positive finite e.
+ * frexp gives 2 alpha e = m 2^E with m in [0.5, 1), so floor(log2) = E - 1. */
+double or_delta(double e, double alpha) {
+  int E;
+  double v = 2.0 * alpha * e;
+  (void)frexp(v, &E);
+  return ldexp(1.0, E - 1);
+}
+
+/* Round-half-even of the exact real (x - xh) / delta, for finite x, xh.
+ * d = fl(x - xh) and err with d + err == x - xh exactly (Knuth's TwoSum).
+ * Rounding is monotone, so d lies on the same side of every representable
+ * tie point (m + 1/2) delta as the exact difference, or on it; on a tie the
+ * sign of err breaks it, and only err == 0 is a true tie (even wins).
+ * Returns the integer as a double (may be far outside the int16 range). */
+double or_round_residual(double x, double xh, double delta) {
+  double d = x - xh;
+  double bb = d - x;
+  double err = (x - (d - bb)) + (-xh - bb);
+  double t = d / delta; /* exact: delta is a power of two */
+  double fl = floor(t);
+  double mid = fl + 0.5; /* exact for |t| < 2^51; larger t escape anyway */
+  if (t > mid) return fl + 1.0;
+  if (t < mid) return fl;
+  /* t == mid: the rounded difference sits exactly on a tie */
+  if (err > 0.0) return fl + 1.0;
+  if (err < 0.0) return fl;
+  return (fmod(fl, 2.0) == 0.0) ? fl : fl + 1.0;
+}
+
+/* Is 0 strictly nearer to x >= 0 than the grid level g = xh + qd (exact reals)?
+ * For x >= 0 that holds iff g < 0 or g > 2x.  gs = fl(xh + qd) and ge with
+ * gs + ge == g exactly (TwoSum); rounding is monotone and 0, 2x are
+ * representable, so gs decides both comparisons except gs == 2x, where the
+ * sign of ge does (gs == 0 means g == 0 exactly). */
+static int zero_is_nearer(double x, double xh, double qd) {
+  double gs = xh + qd;
+  double bb = gs - xh;
+  double ge = (xh - (gs - bb)) + (qd - bb);
+  double two_x = 2.0 * x;
+  if (gs < 0.0) return 1;
+  if (gs > two_x) return 1;
+  if (gs == two_x && ge > 0.0) return 1;
+  return 0;
+}
+
+/* Quantize one histogram against xhat.  Writes codes, x' (raw x at escapes)
+ * and returns status bits (ZERO_IMAGE / NONFINITE_INPUT / CODE_ESCAPE /
+ * AE_EXACT).  *scale = max(x), *delta = bin width (0 for a zero image).
+ * retry_level r uses alpha / 4^r. */
+static unsigned quantize_one(const double* x, const float* xh, int P, double tau,
+                             double alpha, int retry_level, int16_t* codes,
+                             double* xp, double* scale, double* delta) {
+  unsigned st = 0;
+  double s = 0.0;
+  int bad = 0;
+  for (int p = 0; p < P; ++p) {
+    if (!isfinite(x[p]) || x[p] < 0.0) bad = 1;
+    else if (x[p] > s) s = x[p];
+  }
+  *scale = s;
+  if (bad) {
+    *delta = 0.0;
+    for (int p = 0; p < P; ++p) { codes[p] = CODE_ESCAPE; xp[p] = x[p]; }
+    return ST_NONFINITE_INPUT | ST_VERBATIM;
+  }
+  if (s == 0.0) {
+    *delta = 0.0;
+    for (int p = 0; p < P; ++p) { codes[p] = 0; xp[p] = 0.0; }
+    return ST_ZERO_IMAGE;
+  }
+  double a = alpha;
+  for (int r = 0; r < retry_level; ++r) a *= 0.25;
+  double e = tau * s;
+  double dl = or_delta(e, a);
+  *delta = dl;
+  int allzero = 1;
+  for (int p = 0; p < P; ++p) {
+    double xhv = (double)xh[p];
+    if (!isfinite(xhv)) {
+      codes[p] = CODE_ESCAPE; xp[p] = x[p]; st |= ST_CODE_ESCAPE; allzero = 0;
+      continue;
+    }
+    double q = or_round_residual(x[p], xhv, dl);
+    if (q > (double)CODE_MAX || q < -(double)CODE_MAX) {
+      codes[p] = CODE_ESCAPE; xp[p] = x[p]; st |= ST_CODE_ESCAPE; allzero = 0;
+      continue;
+    }
+    if (zero_is_nearer(x[p], xhv, q * dl)) {
+      codes[p] = CODE_ZERO; xp[p] = 0.0; allzero = 0;
+      continue;
+    }
+    codes[p] = (int16_t)q;
+    if (q != 0.0) allzero = 0;
+    xp[p] = xhv + q * dl; /* q * dl is exact; the sum is rounded once */
+  }
+  if (allzero) st |= ST_AE_EXACT;
+  return st;
+}
+
+void or_quantize(const double* x, const float* xhat, int64_t ld, int64_t n, int P,
+                 double tau, double alpha, int16_t* codes, double* xprime,
+                 double* scale, double* delta, uint16_t* status) {
+#pragma omp parallel for schedule(static)
+  for (int64_t b = 0; b < n; ++b)
+    status[b] = (uint16_t)quantize_one(x + (size_t)b * P, xhat + (size_t)b * ld, P,
+                                       tau, alpha, 0, codes + (size_t)b * P,
+                                       xprime + (size_t)b * P, scale + b, delta + b);
+}
+
+/* Dequantize: x' = fl(xhat + q delta), 0 at the zero code, raw value at escapes. */
+void or_dequantize(const float* xhat, int64_t ld, const int16_t* codes,
+                   const double* raw, const double* delta, int64_t n, int P,
+                   double* xprime) {
+  for (int64_t b = 0; b < n; ++b)
+    for (int p = 0; p < P; ++p) {
+      size_t o = (size_t)b * P + p;
+      if (codes[o] == CODE_ESCAPE) { xprime[o] = raw[o]; continue; }
+      if (codes[o] == CODE_ZERO) { xprime[o] = 0.0; continue; }
+      xprime[o] = (double)xhat[(size_t)b * ld + p] + (double)codes[o] * delta[b];
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Stage 5: constraint satisfaction by Newton on the dual, Eq. (6)            */
+/* ------------------------------------------------------------------------- */
+
+/* f(lambda) for the chosen loss. */
+static void corrected_one(const or_grid* g, const double* xp, const double lam[4],
+                          int loss, double* f) {
+  for (int j = 0; j < g->n_perp; ++j)
+    for (int i = 0; i < g->n_par; ++i) {
+      size_t o = (size_t)j * g->n_par + i;
+      double lp = lam[0] * phi_at(g, 0, j, i) + lam[1] * phi_at(g, 1, j, i) +
+                  lam[2] * phi_at(g, 2, j, i) + lam[3] * phi_at(g, 3, j, i);
+      f[o] = loss == 1 ? xp[o] - lp : xp[o] * exp(-lp);
+    }
+}
+
+/* Scaled residual max_k |g_k| / S_k; non-finite on failure. */
+static double scaled_residual(const double gk[4], const double S[4]) {
+  double r = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    if (!isfinite(gk[k]) || !isfinite(S[k])) return NAN;
+    double den = S[k] > 0.0 ? S[k] : 1e-300;
+    double v = fabs(gk[k]) / den;
+    if (v > r) r = v;
+  }
+  return r;
+}
+
+/* M_kl = sum vol phi_k phi_l w, with w = f (KL) or 1 (L2). */
+static void jacobian_one(const or_grid* g, const double* f, int loss, double M[16]) {
+  for (int a = 0; a < 16; ++a) M[a] = 0.0;
+  for (int j = 0; j < g->n_perp; ++j)
+    for (int i = 0; i < g->n_par; ++i) {
+      double w = vol_at(g, j, i) * (loss == 1 ? 1.0 : f[(size_t)j * g->n_par + i]);
+      for (int k = 0; k < 4; ++k)
+        for (int l = 0; l < 4; ++l)
+          M[4 * k + l] += w * phi_at(g, k, j, i) * phi_at(g, l, j, i);
+    }
+}
+
+/* Solve M d = r for symmetric positive definite M by Cholesky.
+ * Returns 0 on success, -1 if M is not numerically positive definite. */
+int or_cholesky_solve4(const double M[16], const double r[4], double d[4]) {
+  double L[16] = {0};
+  for (int k = 0; k < 4; ++k) {
+    for (int l = 0; l <= k; ++l) {
+      double s = M[4 * k + l];
+      for (int m = 0; m < l; ++m) s -= L[4 * k + m] * L[4 * l + m];
+      if (k == l) {
+        if (!(s > 0.0)) return -1;
+        L[4 * k + k] = sqrt(s);
+      } else {
+        L[4 * k + l] = s / L[4 * l + l];
+      }
+    }
+  }
+  double y[4];
+  for (int k = 0; k < 4; ++k) {
+    double s = r[k];
+    for (int m = 0; m < k; ++m) s -= L[4 * k + m] * y[m];
+    y[k] = s / L[4 * k + k];
+  }
+  for (int k = 3; k >= 0; --k) {
+    double s = y[k];
+    for (int m = k + 1; m < 4; ++m) s -= L[4 * m + k] * d[m];
+    d[k] = s / L[4 * k + k];
+  }
+  for (int k = 0; k < 4; ++k)
+    if (!isfinite(d[k])) return -1;
+  return 0;
+}
+
+/* Residual g = A f - Q and scale S at lambda; returns the scaled residual. */
+static double residual_at(const or_grid* g, const double* xp, const double* Q,
+                          const double lam[4], int loss, double* f, double gk[4],
+                          double S[4]) {
+  corrected_one(g, xp, lam, loss, f);
+  double Af[4];
+  moments_one(g, f, Af);
+  abs_moments_one(g, f, S);
+  for (int k = 0; k < 4; ++k) gk[k] = Af[k] - Q[k];
+  return scaled_residual(gk, S);
+}
+
+/* Dual objective to minimise, psi(lambda) = sum vol x' e^{-lambda.phi} + lambda.Q
+ * (KL loss); its gradient is -g and its Hessian M, so Eq. (6) with the
+ * dual's Hessian H = -M reads lambda <- lambda + s M^{-1} g. */
+static double psi_at(const or_grid* g, const double* f, const double* Q,
+                     const double lam[4]) {
+  double s = 0.0;
+  for (int j = 0; j < g->n_perp; ++j)
+    for (int i = 0; i < g->n_par; ++i)
+      s += vol_at(g, j, i) * f[(size_t)j * g->n_par + i];
+  return s + lam[0] * Q[0] + lam[1] * Q[1] + lam[2] * Q[2] + lam[3] * Q[3];
+}
+
+/* Round 1: plain Newton, Eq. (6), step s, at most max_iter steps, starting at
+ * lam (in/out).  Convergence is tested before each step.  Returns 1 if
+ * converged, 0 otherwise; *iters counts the steps taken. */
+static int newton_round1(const or_grid* g, const double* xp, const double* Q,
+                         double lam[4], int max_iter, double step_s, double tol,
+                         int loss, double* f, int* iters) {
+  double gk[4], S[4], M[16], d[4];
+  for (int it = 0;; ++it) {
+    double r = residual_at(g, xp, Q, lam, loss, f, gk, S);
+    *iters = it;
+    if (!isfinite(r)) return 0;
+    if (r <= tol) return 1;
+    if (it == max_iter) return 0;
+    jacobian_one(g, f, loss, M);
+    if (or_cholesky_solve4(M, gk, d) != 0) return 0;
+    for (int k = 0; k < 4; ++k) lam[k] += step_s * d[k];
+  }
+}
+
+/* Round 2: damped Newton from zero.  A step t in {1, 1/2, 1/4, ...} is taken
+ * when it decreases psi by the Armijo amount, or, once psi's change drowns
+ * in rounding, when it lowers the scaled residual. */
+static int newton_round2(const or_grid* g, const double* xp, const double* Q,
+                         double lam[4], int max_iter, double tol, int loss,
+                         double* f, double* ftry, int* iters) {
+  double gk[4], S[4], M[16], d[4];
+  for (int k = 0; k < 4; ++k) lam[k] = 0.0;
+  for (int it = 0;; ++it) {
+    double r = residual_at(g, xp, Q, lam, loss, f, gk, S);
+    *iters = it;
+    if (!isfinite(r)) return 0;
+    if (r <= tol) return 1;
+    if (it == max_iter) return 0;
+    jacobian_one(g, f, loss, M);
+    if (or_cholesky_solve4(M, gk, d) != 0) return 0;
+    double psi0 = psi_at(g, f, Q, lam);
+    double slope = gk[0] * d[0] + gk[1] * d[1] + gk[2] * d[2] + gk[3] * d[3];
+    double t = 1.0;
+    int accepted = 0;
+    for (int h = 0; h < 40; ++h, t *= 0.5) {
+      double lt[4], gt[4], St[4];
+      for (int k = 0; k < 4; ++k) lt[k] = lam[k] + t * d[k];
+      double rt = residual_at(g, xp, Q, lt, loss, ftry, gt, St);
+      if (!isfinite(rt)) continue;
+      double psit = psi_at(g, ftry, Q, lt);
+      if (psit <= psi0 - 1e-4 * t * slope || rt <= (1.0 - 0.5 * t) * r) {
+        for (int k = 0; k < 4; ++k) lam[k] = lt[k];
+        accepted = 1;
+        break;
+      }
+    }
+    if (!accepted) return 0;
+  }
+}
+
+/* Newton driver for one histogram (rounds 1 and 2, optional warm start).
+ * lam in: warm start (used when warm != 0) ; out: multipliers.
+ * Returns status bits CONVERGED / ROUND2 / WARM_REJECTED; 0 if neither round
+ * converged.  *iters = total steps taken. */
+static unsigned newton_one(const or_grid* g, const double* xp, const double* Q,
+                           double lam[4], int warm, const or_params* pr,
+                           double* f, double* ftry, int* iters) {
+  unsigned st = 0;
+  int it1 = 0, it2 = 0, itw = 0, conv;
+  if (warm) {
+    double gk[4], S[4];
+    double r0 = residual_at(g, xp, Q, lam, pr->loss, f, gk, S);
+    conv = newton_round1(g, xp, Q, lam, pr->warm_iters, pr->step_s, pr->tol,
+                         pr->loss, f, &itw);
+    double rw = residual_at(g, xp, Q, lam, pr->loss, f, gk, S);
+    if (conv) { *iters = itw; return ST_CONVERGED; }
+    if (!isfinite(rw) || !isfinite(r0) || rw > pr->warm_reject || rw > r0) {
+      st |= ST_WARM_REJECTED;
+      for (int k = 0; k < 4; ++k) lam[k] = 0.0;
+      conv = newton_round1(g, xp, Q, lam, pr->max_iter, pr->step_s, pr->tol,
+                           pr->loss, f, &it1);
+    } else {
+      conv = newton_round1(g, xp, Q, lam, pr->max_iter - pr->warm_iters,
+                           pr->step_s, pr->tol, pr->loss, f, &it1);
+    }
+  } else {
+    for (int k = 0; k < 4; ++k) lam[k] = 0.0;
+    conv = newton_round1(g, xp, Q, lam, pr->max_iter, pr->step_s, pr->tol,
+                         pr->loss, f, &it1);
+  }
+  if (conv) {
+    *iters = itw + it1;
+    return st | ST_CONVERGED;
+  }
+  conv = newton_round2(g, xp, Q, lam, pr->r2_max_iter, pr->tol, pr->loss, f, ftry, &it2);
+  *iters = itw + it1 + it2;
+  if (conv) return st | ST_ROUND2;
+  return st | ST_ROUND2 | 0x8000u; /* internal: not converged */
+}
+
+/* Round 1 alone (plain steps of Eq. (6) from lam, at most pr->max_iter).
+ * conv[b] = 1 if converged.  Used to pin single Newton steps. */
+void or_newton_round1(const or_grid* g, const double* xprime, const double* Q, int64_t n,
+                      const or_params* pr, double* lam, int32_t* iters, int32_t* conv) {
+  const size_t P = (size_t)g->n_par * g->n_perp;
+  double* f = (double*)malloc(P * sizeof(double));
+  for (int64_t b = 0; b < n; ++b) {
+    int it = 0;
+    conv[b] = newton_round1(g, xprime + b * P, Q + 4 * b, lam + 4 * b, pr->max_iter,
+                            pr->step_s, pr->tol, pr->loss, f, &it);
+    iters[b] = it;
+  }
+  free(f);
+}
+
+/* Newton only (qoi_correct): x' and targets Q given.  lam in/out. */
+void or_newton(const or_grid* g, const double* xprime, const double* Q, int64_t n,
+               const or_params* pr, int warm, double* lam, double* f_out,
+               int32_t* iters, uint16_t* status) {
+  const size_t P = (size_t)g->n_par * g->n_perp;
+#pragma omp parallel
+  {
+    double* f = (double*)malloc(P * sizeof(double));
+    double* ft = (double*)malloc(P * sizeof(double));
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t b = 0; b < n; ++b) {
+      int it = 0;
+      unsigned st = newton_one(g, xprime + b * P, Q + 4 * b, lam + 4 * b, warm, pr, f, ft, &it);
+      if (f_out) memcpy(f_out + b * P, f, P * sizeof(double));
+      iters[b] = it;
+      status[b] = (uint16_t)(st & 0xffffu);
+    }
+    free(f);
+    free(ft);
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Stages 4+5 end to end for one histogram given the decoded xhat             */
+/* ------------------------------------------------------------------------- */
+
+/* Targets Q from x, quantize against xhat, Newton, then the end-to-end check
+ * (|f - x| <= e at every point and the moments within qoi_check).  On a
+ * failed check: one retry with alpha/4; then verbatim.  Outputs codes, lam,
+ * scale, iters, status and (optionally) f. */
+void or_compress_correct(const or_grid* g, const double* x, const float* xhat,
+                         int64_t ld, int64_t n, const or_params* pr,
+                         const double* lam0 /* NULL: start from zero */,
+                         int16_t* codes, double* lam, double* scale, int32_t* iters,
+                         uint16_t* status, double* f_out) {
+  const int P = g->n_par * g->n_perp;
+#pragma omp parallel
+  {
+    double* xp = (double*)malloc((size_t)P * sizeof(double));
+    double* f = (double*)malloc((size_t)P * sizeof(double));
+    double* ft = (double*)malloc((size_t)P * sizeof(double));
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t b = 0; b < n; ++b) {
+      const double* xb = x + (size_t)b * P;
+      int16_t* cb = codes + (size_t)b * P;
+      double* lb = lam + 4 * b;
+      double Q[4], S[4], delta = 0.0;
+      unsigned st = 0;
+      int total_it = 0, done = 0;
+      for (int level = 0; level < 2 && !done; ++level) {
+        unsigned qs = quantize_one(xb, xhat + (size_t)b * ld, P, pr->tau, pr->alpha,
+                                   level, cb, xp, scale + b, &delta);
+        st = qs | (level ? ST_ALPHA_RETRY : 0u) | (st & ST_WARM_REJECTED);
+        if (qs & (ST_NONFINITE_INPUT | ST_ZERO_IMAGE)) {
+          for (int k = 0; k < 4; ++k) lb[k] = 0.0;
+          for (int p = 0; p < P; ++p) f[p] = xp[p];
+          done = 1;
+          break;
+        }
+        moments_one(g, xb, Q);
+        int warm = (lam0 != NULL) && level == 0;
+        if (warm) for (int k = 0; k < 4; ++k) lb[k] = lam0[4 * b + k];
+        int it = 0;
+        unsigned ns = newton_one(g, xp, Q, lb, warm, pr, f, ft, &it);
+        total_it += it;
+        st |= ns & 0x7fffu;
+        if (ns & 0x8000u) break; /* neither round converged: verbatim */
+        /* end-to-end check on the corrected histogram */
+        double e = pr->tau * scale[b];
+        int ok = 1;
+        for (int p = 0; p < P; ++p)
+          if (!(fabs(f[p] - xb[p]) <= e)) { ok = 0; break; }
+        if (ok) {
+          double Qf[4];
+          moments_one(g, f, Qf);
+          abs_moments_one(g, xb, S);
+          for (int k = 0; k < 4; ++k) {
+            double den = S[k] > 0.0 ? S[k] : 1e-300;
+            if (!(fabs(Qf[k] - Q[k]) / den <= pr->qoi_check)) ok = 0;
+          }
+        }
+        if (ok) done = 1;
+      }
+      if (!done) {
+        /* verbatim: every point stored raw, no correction */
+        st = (st & ST_WARM_REJECTED) | ST_VERBATIM | (st & ST_ALPHA_RETRY) |
+             (st & ST_ROUND2);
+        for (int p = 0; p < P; ++p) { cb[p] = CODE_ESCAPE; f[p] = xb[p]; }
+        for (int k = 0; k < 4; ++k) lb[k] = 0.0;
+      }
+      if (st & ST_ZERO_IMAGE) {
+        for (int p = 0; p < P; ++p) f[p] = 0.0;
+      }
+      iters[b] = total_it;
+      status[b] = (uint16_t)st;
+      if (f_out) memcpy(f_out + (size_t)b * P, f, (size_t)P * sizeof(double));
+    }
+    free(xp);
+    free(f);
+    free(ft);
+  }
+}
+
+/* Decompression (Sec. III, end of Stage 5): x' = fl(xhat + q delta) (0 at the
+ * zero code, raw value at escapes), then f = x' e^{-lambda.phi} everywhere. */
+void or_decompress(const or_grid* g, const float* xhat, int64_t ld,
+                   const int16_t* codes, const double* raw, const double* scale,
+                   const double* lam, const uint16_t* status, int64_t n,
+                   const or_params* pr, double* f) {
+  const int P = g->n_par * g->n_perp;
+  for (int64_t b = 0; b < n; ++b) {
+    double* fb = f + (size_t)b * P;
+    if (status[b] & ST_ZERO_IMAGE) {
+      for (int p = 0; p < P; ++p) fb[p] = 0.0;
+      continue;
+    }
+    double delta = 0.0;
+    if (!(status[b] & (ST_VERBATIM | ST_NONFINITE_INPUT))) {
+      double a = pr->alpha;
+      if (status[b] & ST_ALPHA_RETRY) a *= 0.25;
+      delta = or_delta(pr->tau * scale[b], a);
+    }
+    for (int j = 0; j < g->n_perp; ++j)
+      for (int i = 0; i < g->n_par; ++i) {
+        size_t o = (size_t)j * g->n_par + i, ob = (size_t)b * P + o;
+        double xp;
+        if (codes[ob] == CODE_ESCAPE) xp = raw[ob];
+        else if (codes[ob] == CODE_ZERO) xp = 0.0;
+        else xp = (double)xhat[(size_t)b * ld + o] + (double)codes[ob] * delta;
+        const double* l = lam + 4 * b;
+        double lp = l[0] * phi_at(g, 0, j, i) + l[1] * phi_at(g, 1, j, i) +
+                    l[2] * phi_at(g, 2, j, i) + l[3] * phi_at(g, 3, j, i);
+        fb[o] = pr->loss == 1 ? xp - lp : xp * exp(-lp);
+      }
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. (7): NRMSE                                                             */
+/* ------------------------------------------------------------------------- */
+
+double or_nrmse(const double* u, const double* f, int64_t N) {
+  double mx = -INFINITY, mn = INFINITY, s = 0.0;
+  for (int64_t t = 0; t < N; ++t) {
+    double d = u[t] - f[t];
+    s += d * d;
+    if (u[t] > mx) mx = u[t];
+    if (u[t] < mn) mn = u[t];
+  }
+  return sqrt(s / (double)N) / (mx - mn);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Stages 2-3: autoencoder (dense layers y = W^T x + b), FP64                 */
+/* ------------------------------------------------------------------------- */
+
+/* Weights: W1 [P][H], b1 [H], W2 [H][L], b2 [L], b3 [H], b4 [P];
+ * tied: decoder layer 3 uses W2^T, layer 4 uses W1^T (Sec. IV-B);
+ * untied: W3 [L][H], W4 [H][P].  act: 0 identity (the paper's linear
+ * activation), 1 ReLU.  Normalisation u = (x / s - mu) / sigma with
+ * s = max(x) per histogram and per-pixel mu, sigma. */
+typedef struct {
+  int P, H, L, tied, act;
+  const double *W1, *b1, *W2, *b2, *W3, *b3, *W4, *b4, *mu, *sigma;
+} or_ae;
+
+static double act_f(int act, double v) { return act == 1 ? (v > 0.0 ? v : 0.0) : v; }
+static double act_d(int act, double pre) { return act == 1 ? (pre > 0.0 ? 1.0 : 0.0) : 1.0; }
+
+/* Dense layer y[o] = sum_k W[k][o] x[k] + b[o] (W stored [in][out]). */
+static void dense(const double* W, const double* b, const double* x, int nin, int nout,
+                  double* y) {
+  for (int o = 0; o < nout; ++o) {
+    double s = 0.0;
+    for (int k = 0; k < nin; ++k) s += W[(size_t)k * nout + o] * x[k];
+    y[o] = s + b[o];
+  }
+}
+
+/* Dense layer with the transposed weight: y[o] = sum_k W[o][k] x[k] + b[o]. */
+static void dense_t(const double* W, const double* b, const double* x, int nin, int nout,
+                    double* y) {
+  for (int o = 0; o < nout; ++o) {
+    double s = 0.0;
+    for (int k = 0; k < nin; ++k) s += W[(size_t)o * nin + k] * x[k];
+    y[o] = s + b[o];
+  }
+}
+
+static double image_scale(const double* x, int P) {
+  double s = 0.0;
+  for (int p = 0; p < P; ++p)
+    if (x[p] > s) s = x[p];
+  return s;
+}
+
+/* Forward pass of one histogram; fills u (normalised input), pre1/h1, z,
+ * pre3/h3, y (normalised output).  Returns the scale s. */
+static double ae_forward_one(const or_ae* m, const double* x, double* u, double* pre1,
+                             double* h1, double* z, double* pre3, double* h3, double* y) {
+  double s = image_scale(x, m->P);
+  double inv = (s > 0.0 && isfinite(s)) ? 1.0 / s : 0.0;
+  for (int p = 0; p < m->P; ++p) u[p] = (x[p] * inv - m->mu[p]) / m->sigma[p];
+  dense(m->W1, m->b1, u, m->P, m->H, pre1);
+  for (int h = 0; h < m->H; ++h) h1[h] = act_f(m->act, pre1[h]);
+  dense(m->W2, m->b2, h1, m->H, m->L, z);
+  if (m->tied) dense_t(m->W2, m->b3, z, m->L, m->H, pre3);
+  else dense(m->W3, m->b3, z, m->L, m->H, pre3);
+  for (int h = 0; h < m->H; ++h) h3[h] = act_f(m->act, pre3[h]);
+  if (m->tied) dense_t(m->W1, m->b4, h3, m->H, m->P, y);
+  else dense(m->W4, m->b4, h3, m->H, m->P, y);
+  return s;
+}
+
+/* Encode + decode: latent [n][L], xhat [n][P] = s (sigma y + mu), scale [n]. */
+void or_ae_forward(const or_ae* m, const double* x, int64_t n, double* latent,
+                   double* xhat, double* scale) {
+#pragma omp parallel
+  {
+    int P = m->P, H = m->H, L = m->L;
+    double* buf = (double*)malloc(sizeof(double) * (size_t)(3 * P + 4 * H + L));
+    double *u = buf, *y = buf + P, *pre1 = buf + 2 * P, *h1 = pre1 + H, *pre3 = h1 + H,
+           *h3 = pre3 + H, *z = h3 + H;
+#pragma omp for schedule(static)
+    for (int64_t b = 0; b < n; ++b) {
+      double s = ae_forward_one(m, x + (size_t)b * P, u, pre1, h1, z, pre3, h3, y);
+      scale[b] = s;
+      for (int l = 0; l < L; ++l) latent[(size_t)b * L + l] = z[l];
+      for (int p = 0; p < P; ++p)
+        xhat[(size_t)b * P + p] = s * (m->sigma[p] * y[p] + m->mu[p]);
+    }
+    free(buf);
+  }
+}
+
+/* Decode only, from a stored latent: xhat = s (sigma y + mu). */
+void or_ae_decode(const or_ae* m, const double* latent, const double* scale, int64_t n,
+                  double* xhat) {
+  int P = m->P, H = m->H, L = m->L;
+  double* pre3 = (double*)malloc(sizeof(double) * (size_t)(2 * H + P));
+  double *h3 = pre3 + H, *y = h3 + H;
+  for (int64_t b = 0; b < n; ++b) {
+    const double* z = latent + (size_t)b * L;
+    if (m->tied) dense_t(m->W2, m->b3, z, L, H, pre3);
+    else dense(m->W3, m->b3, z, L, H, pre3);
+    for (int h = 0; h < H; ++h) h3[h] = act_f(m->act, pre3[h]);
+    if (m->tied) dense_t(m->W1, m->b4, h3, H, P, y);
+    else dense(m->W4, m->b4, h3, H, P, y);
+    for (int p = 0; p < P; ++p)
+      xhat[(size_t)b * P + p] = scale[b] * (m->sigma[p] * y[p] + m->mu[p]);
+  }
+  free(pre3);
+}
+
+/* Eq. (5): loss = mean over the batch and the P pixels of (y - u)^2 in the
+ * normalised space, and its gradient with respect to every parameter
+ * (gradients have the parameters' shapes; tied weights receive the sum of
+ * their encoder and decoder uses).  Returns the loss. */
+double or_ae_loss_grad(const or_ae* m, const double* x, int64_t B, double* gW1,
+                       double* gb1, double* gW2, double* gb2, double* gW3, double* gb3,
+                       double* gW4, double* gb4) {
+  int P = m->P, H = m->H, L = m->L;
+  memset(gW1, 0, sizeof(double) * (size_t)P * H);
+  memset(gb1, 0, sizeof(double) * H);
+  memset(gW2, 0, sizeof(double) * (size_t)H * L);
+  memset(gb2, 0, sizeof(double) * L);
+  memset(gb3, 0, sizeof(double) * H);
+  memset(gb4, 0, sizeof(double) * P);
+  if (!m->tied) {
+    memset(gW3, 0, sizeof(double) * (size_t)L * H);
+    memset(gW4, 0, sizeof(double) * (size_t)H * P);
+  }
+  double* buf = (double*)malloc(sizeof(double) * (size_t)(4 * P + 8 * H + 2 * L));
+  double *u = buf, *y = u + P, *dy = y + P, *pre1 = dy + P, *h1 = pre1 + H, *pre3 = h1 + H,
+         *h3 = pre3 + H, *dh3 = h3 + H, *dpre3 = dh3 + H, *dh1 = dpre3 + H,
+         *dpre1 = dh1 + H, *z = dpre1 + H, *dz = z + L;
+  double loss = 0.0, norm = 1.0 / ((double)B * P);
+  for (int64_t b = 0; b < B; ++b) {
+    ae_forward_one(m, x + (size_t)b * P, u, pre1, h1, z, pre3, h3, y);
+    for (int p = 0; p < P; ++p) {
+      double d = y[p] - u[p];
+      loss += d * d;
+      dy[p] = 2.0 * d * norm;
+    }
+    /* layer 4: y = W4^T h3 + b4 */
+    for (int p = 0; p < P; ++p) gb4[p] += dy[p];
+    for (int h = 0; h < H; ++h) {
+      double s = 0.0;
+      for (int p = 0; p < P; ++p) {
+        double w = m->tied ? m->W1[(size_t)p * H + h] : m->W4[(size_t)h * P + p];
+        s += w * dy[p];
+        if (m->tied) gW1[(size_t)p * H + h] += dy[p] * h3[h];
+        else gW4[(size_t)h * P + p] += h3[h] * dy[p];
+      }
+      dh3[h] = s;
+      dpre3[h] = s * act_d(m->act, pre3[h]);
+    }
+    /* layer 3: pre3 = W3^T z + b3 */
+    for (int h = 0; h < H; ++h) gb3[h] += dpre3[h];
+    for (int l = 0; l < L; ++l) {
+      double s = 0.0;
+      for (int h = 0; h < H; ++h) {
+        double w = m->tied ? m->W2[(size_t)h * L + l] : m->W3[(size_t)l * H + h];
+        s += w * dpre3[h];
+        if (m->tied) gW2[(size_t)h * L + l] += dpre3[h] * z[l];
+        else gW3[(size_t)l * H + h] += z[l] * dpre3[h];
+      }
+      dz[l] = s;
+    }
+    /* layer 2: z = W2^T h1 + b2 */
+    for (int l = 0; l < L; ++l) gb2[l] += dz[l];
+    for (int h = 0; h < H; ++h) {
+      double s = 0.0;
+      for (int l = 0; l < L; ++l) {
+        s += m->W2[(size_t)h * L + l] * dz[l];
+        gW2[(size_t)h * L + l] += h1[h] * dz[l];
+      }
+      dh1[h] = s;
+      dpre1[h] = s * act_d(m->act, pre1[h]);
+    }
+    /* layer 1: pre1 = W1^T u + b1 */
+    for (int h = 0; h < H; ++h) gb1[h] += dpre1[h];
+    for (int p = 0; p < P; ++p)
+      for (int h = 0; h < H; ++h) gW1[(size_t)p * H + h] += u[p] * dpre1[h];
+  }
+  free(buf);
+  return loss * norm;
+}
+
+/* Adam (Kingma & Ba) on one parameter array: t is the 1-based step. */
+void or_adam(double* w, const double* gr, double* mom1, double* mom2, int64_t cnt,
+             double lr, double beta1, double beta2, double eps, int t) {
+  double c1 = 1.0 - pow(beta1, t), c2 = 1.0 - pow(beta2, t);
+  for (int64_t a = 0; a < cnt; ++a) {
+    mom1[a] = beta1 * mom1[a] + (1.0 - beta1) * gr[a];
+    mom2[a] = beta2 * mom2[a] + (1.0 - beta2) * gr[a] * gr[a];
+    double mh = mom1[a] / c1, vh = mom2[a] / c2;
+    w[a] -= lr * mh / (sqrt(vh) + eps);
+  }
+}
+
+/* Z-score statistics of x / max(x) per pixel over a training set:
+ * mu_p = mean, sigma_p = max(std, floor). */
+void or_fit_normalizer(const double* x, int64_t n, int P, double floor_sigma,
+                       double* mu, double* sigma) {
+  for (int p = 0; p < P; ++p) { mu[p] = 0.0; sigma[p] = 0.0; }
+  for (int64_t b = 0; b < n; ++b) {
+    double s = image_scale(x + (size_t)b * P, P);
+    double inv = s > 0.0 ? 1.0 / s : 0.0;
+    for (int p = 0; p < P; ++p) mu[p] += x[(size_t)b * P + p] * inv;
+  }
+  for (int p = 0; p < P; ++p) mu[p] /= (double)n;
+  for (int64_t b = 0; b < n; ++b) {
+    double s = image_scale(x + (size_t)b * P, P);
+    double inv = s > 0.0 ? 1.0 / s : 0.0;
+    for (int p = 0; p < P; ++p) {
+      double d = x[(size_t)b * P + p] * inv - mu[p];
+      sigma[p] += d * d;
+    }
+  }
+  for (int p = 0; p < P; ++p) {
+    double sd = sqrt(sigma[p] / (double)n);
+    sigma[p] = sd > floor_sigma ? sd : floor_sigma;
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Learned warm start: a 3-layer MLP in -> 64 -> 64 -> 4 with ReLU            */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+  int nin, nh, nout;
+  const double *W1, *b1, *W2, *b2, *W3, *b3; /* [in][out] layouts */
+  const double *in_mu, *in_sd, *out_mu, *out_sd;
+} or_mlp;
+
+static void mlp_fwd_one(const or_mlp* m, const double* in, double* u, double* a1,
+                        double* h1, double* a2, double* h2, double* o) {
+  for (int k = 0; k < m->nin; ++k) u[k] = (in[k] - m->in_mu[k]) / m->in_sd[k];
+  dense(m->W1, m->b1, u, m->nin, m->nh, a1);
+  for (int h = 0; h < m->nh; ++h) h1[h] = a1[h] > 0.0 ? a1[h] : 0.0;
+  dense(m->W2, m->b2, h1, m->nh, m->nh, a2);
+  for (int h = 0; h < m->nh; ++h) h2[h] = a2[h] > 0.0 ? a2[h] : 0.0;
+  dense(m->W3, m->b3, h2, m->nh, m->nout, o);
+}
+
+/* Prediction in physical units: lambda = out * out_sd + out_mu. */
+void or_mlp_predict(const or_mlp* m, const double* in, int64_t n, double* lam) {
+  int nin = m->nin, nh = m->nh, no = m->nout;
+  double* buf = (double*)malloc(sizeof(double) * (size_t)(nin + 4 * nh + no));
+  double *u = buf, *a1 = u + nin, *h1 = a1 + nh, *a2 = h1 + nh, *h2 = a2 + nh, *o = h2 + nh;
+  for (int64_t b = 0; b < n; ++b) {
+    mlp_fwd_one(m, in + (size_t)b * nin, u, a1, h1, a2, h2, o);
+    for (int k = 0; k < no; ++k) lam[(size_t)b * no + k] = o[k] * m->out_sd[k] + m->out_mu[k];
+  }
+  free(buf);
+}
+
+/* Loss = mean over batch and outputs of (out - t)^2 with t the normalised
+ * target (lambda - out_mu) / out_sd; gradients for all six arrays. */
+double or_mlp_loss_grad(const or_mlp* m, const double* in, const double* target,
+                        int64_t B, double* gW1, double* gb1, double* gW2, double* gb2,
+                        double* gW3, double* gb3) {
+  int nin = m->nin, nh = m->nh, no = m->nout;
+  memset(gW1, 0, sizeof(double) * (size_t)nin * nh);
+  memset(gb1, 0, sizeof(double) * nh);
+  memset(gW2, 0, sizeof(double) * (size_t)nh * nh);
+  memset(gb2, 0, sizeof(double) * nh);
+  memset(gW3, 0, sizeof(double) * (size_t)nh * no);
+  memset(gb3, 0, sizeof(double) * no);
+  double* buf = (double*)malloc(sizeof(double) * (size_t)(nin + 6 * nh + 2 * no));
+  double *u = buf, *a1 = u + nin, *h1 = a1 + nh, *a2 = h1 + nh, *h2 = a2 + nh, *o = h2 + nh,
+         *dout = o + no, *dh2 = dout + no, *dh1 = dh2 + nh;
+  double loss = 0.0, norm = 1.0 / ((double)B * no);
+  for (int64_t b = 0; b < B; ++b) {
+    mlp_fwd_one(m, in + (size_t)b * nin, u, a1, h1, a2, h2, o);
+    for (int k = 0; k < no; ++k) {
+      double t = (target[(size_t)b * no + k] - m->out_mu[k]) / m->out_sd[k];
+      double d = o[k] - t;
+      loss += d * d;
+      dout[k] = 2.0 * d * norm;
+      gb3[k] += dout[k];
+    }
+    for (int h = 0; h < nh; ++h) {
+      double s = 0.0;
+      for (int k = 0; k < no; ++k) {
+        s += m->W3[(size_t)h * no + k] * dout[k];
+        gW3[(size_t)h * no + k] += h2[h] * dout[k];
+      }
+      dh2[h] = a2[h] > 0.0 ? s : 0.0;
+    }
+    for (int h = 0; h < nh; ++h) gb2[h] += dh2[h];
+    for (int h = 0; h < nh; ++h) {
+      double s = 0.0;
+      for (int k = 0; k < nh; ++k) {
+        s += m->W2[(size_t)h * nh + k] * dh2[k];
+        gW2[(size_t)h * nh + k] += h1[h] * dh2[k];
+      }
+      dh1[h] = a1[h] > 0.0 ? s : 0.0;
+    }
+    for (int h = 0; h < nh; ++h) gb1[h] += dh1[h];
+    for (int k = 0; k < nin; ++k)
+      for (int h = 0; h < nh; ++h) gW1[(size_t)k * nh + h] += u[k] * dh1[h];
+  }
+  free(buf);
+  return loss * norm;
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

@@ -1,0 +1,428 @@
+"""Benchmark of the compress+correct hot path (encode, decode, residual
+quantization, Newton QoI correction, end-to-end check) on seeded synthetic
+velocity-space histograms.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+                  [--config 1] [--n N] [--form plain|fast]
+
+Prints one JSON line (rank 0).  Workload (default): 1,048,576 histograms of
+39 x 39 float64 (12.76 GB, larger than L2, so no flush is needed between
+steps), one autoencoder 1521 -> 256 -> 32 -> 256 -> 1521 trained 2 epochs at
+batch 128, pointwise bound 1e-4 x max, moments to 1e-12.  Under torchrun every
+rank compresses its own shard of that size (weak scaling, no collective on
+the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIGS = {
+    0: dict(name="plain-tiny-64", n=64, H=128, L=16, tau=1e-3, k_max=3, heavy=0.0,
+            epochs=None, steps_train=200, batch=64, dtype="f32"),
+    1: dict(name="plain-scale-1M", n=1_048_576, H=256, L=32, tau=1e-4, k_max=3, heavy=0.0,
+            epochs=2, steps_train=None, batch=128, dtype="f32"),
+    2: dict(name="precision-4M", n=4_194_304, H=512, L=32, tau=1e-4, k_max=4, heavy=0.1,
+            epochs=1, steps_train=None, batch=128, dtype="bf16"),
+}
+METRIC = "compress+correct histograms/s (input GB/s) at QoI err<=1e-10, vs plain form"
+HIST_BYTES = 1521 * 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--n", type=int, default=None, help="override the histogram count")
+    ap.add_argument("--form", default="plain", choices=["plain", "fast"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (torchrun); one process per GPU
+# --------------------------------------------------------------------------
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# workload
+# --------------------------------------------------------------------------
+
+def build_workload(cfg, n, rank, device, aq, synth):
+    import torch
+    seed = synth.config_seed(1) + 1000 * rank
+    x = synth.histograms_torch(n, seed, device, k_max=cfg["k_max"], heavy_frac=cfg["heavy"])
+    P, H, L = synth.P, cfg["H"], cfg["L"]
+    dtype = aq.DTYPE_BF16 if cfg["dtype"] == "bf16" else aq.DTYPE_F32
+    model = aq.Model(P, H, L, tied=True, act=aq.ACT_IDENTITY, dtype=dtype)
+    model.set_group(0, synth.ae_init(P, H, L, seed))
+    model.fit_normalizer(0, x[: min(n, 1 << 16)])
+    B = cfg["batch"]
+    steps = cfg["steps_train"] or (cfg["epochs"] * n // B)
+    ws = None
+    loss = torch.zeros(1, device=device)
+    t0 = time.time()
+    order = torch.randperm(n, generator=torch.Generator().manual_seed(seed)).to(device)
+    xb = torch.empty((B, P), dtype=torch.float64, device=device)
+    for t in range(steps):
+        i0 = (t * B) % max(n - B + 1, 1)
+        torch.index_select(x, 0, order[i0:i0 + B], out=xb) if n > B else xb.copy_(x[:B])
+        ws = model.train_step(xb, lr=1e-3, loss_out=loss, ws=ws)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    return x, model, dict(train_steps=steps, train_s=train_s, train_loss=float(loss.item()))
+
+
+def algorithmic_bytes_fused(P=1521):
+    # read x (float64) and xhat (float32), write codes (int16), lambda, scale,
+    # iters, status
+    return P * 8 + P * 4 + P * 2 + 4 * 8 + 8 + 1 + 2
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2212_10733_gb300 import aeqc, synth
+    aeqc.load()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    cfg = CONFIGS[args.config]
+    n = args.n or cfg["n"]
+    x, model, tr = build_workload(cfg, n, rank, device, aeqc, synth)
+    vpar, vperp, vol = synth.grid_arrays()
+    grid = aeqc.Grid(vpar, vperp, vol)
+    kernel = aeqc.KERNEL_FAST if args.form == "fast" else aeqc.KERNEL_FP64
+    prm = aeqc.params_default(tau=cfg["tau"], kernel=kernel)
+    out = aeqc.Compressed(n, synth.P, cfg["L"], model.latent_dtype(), device, 16 * n)
+    ws = aeqc.compress_batch_workspace(model, n, device)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        aeqc.compress_batch(model, grid, x, prm, out=out, ws=ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ms, world)
+    value = world * n / (ms / 1e3)
+
+    # correctness of the timed outputs (sampled): bound and moments via decompression
+    f = aeqc.decompress_batch(model, grid, out, prm)
+    st = out.status.cpu().numpy()
+    torch.cuda.synchronize()
+    stats = dict(
+        converged_round1=float(np.mean((st & aeqc.ST_CONVERGED) != 0)),
+        verbatim=float(np.mean((st & aeqc.ST_VERBATIM) != 0)),
+        alpha_retry=float(np.mean((st & aeqc.ST_ALPHA_RETRY) != 0)),
+        ae_exact=float(np.mean((st & aeqc.ST_AE_EXACT) != 0)),
+        mean_iters=float(out.iters.float().mean().item()),
+        outliers=int(out.count.item()))
+    e = cfg["tau"] * x.amax(dim=1, keepdim=True)
+    stats["max_err_over_bound"] = float(((f - x).abs() / e).max().item())
+    del f
+
+    # per-stage timing on the same stream, same launch configuration
+    hbuf = torch.empty((n, aeqc.XHAT_LD), dtype=torch.float32, device=device)
+    stage = {}
+    for name, fn in (
+        ("encode", lambda: aeqc.ae_encode(model, x)),
+        ("decode", lambda: aeqc.ae_decode(model, out.latent, out.scale)),
+        ("quantize_correct", lambda: aeqc.quantize_correct(grid, x, hbuf, prm, out=out)),
+    ):
+        if name == "quantize_correct":
+            hbuf.copy_(aeqc.ae_decode(model, out.latent, out.scale))
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(2, args.steps)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        stage[name] = a.elapsed_time(b) / reps
+    del hbuf
+    dom = max(stage, key=stage.get)
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    qc_bytes = algorithmic_bytes_fused() * n
+    achieved = qc_bytes / (stage["quantize_correct"] / 1e3) / 1e9
+    roofline = {"kernel": "quantize_correct (fused quantize + moments + Newton + check)",
+                "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                "peak_source": "measured" if peaks else "fallback",
+                "dominant_stage": dom, "stage_ms": {k: round(v, 3) for k, v in stage.items()}}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+        xh.copy_(x)
+        codes_h = torch.empty(out.codes.shape, dtype=out.codes.dtype, pin_memory=True)
+        lat_h = torch.empty(out.latent.shape, dtype=out.latent.dtype, pin_memory=True)
+        small = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+                 for t in (out.scale, out.lam, out.iters, out.status, out.count)]
+        xdev = torch.empty_like(x)
+
+        def e2e_step():
+            xdev.copy_(xh, non_blocking=True)
+            aeqc.compress_batch(model, grid, xdev, prm, out=out, ws=ws)
+            codes_h.copy_(out.codes, non_blocking=True)
+            lat_h.copy_(out.latent, non_blocking=True)
+            for hdst, src in zip(small, (out.scale, out.lam, out.iters, out.status, out.count)):
+                hdst.copy_(src, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        del x
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(args.steps, 3))
+        a.record(stream)
+        for _ in range(reps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ems = max_over_ranks(a.elapsed_time(b) / reps, world)
+        d2h = codes_h.numel() * 2 + lat_h.numel() * lat_h.element_size() + sum(
+            t.numel() * t.element_size() for t in small)
+        e2e = {"value": round(world * n / (ems / 1e3), 1), "unit": "histograms/s",
+               "ms_per_step": round(ems, 3), "h2d_bytes_per_step": int(xh.numel() * 8),
+               "d2h_bytes_per_step": int(d2h)}
+    launches_per_step = 5
+    res = {
+        "metric": METRIC, "value": round(value, 1), "unit": "histograms/s",
+        "input_gbs": round(value * HIST_BYTES / 1e9, 2),
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 correction / f32 GEMM" if cfg["dtype"] == "f32"
+        else "f64 correction / bf16 GEMM",
+        "data": "synthetic (seeded Gaussian-mixture velocity histograms)",
+        "config": {"workload": cfg["name"], "histograms_per_gpu": n, "grid": "39x39",
+                   "ae": f"1521-{cfg['H']}-{cfg['L']}-{cfg['H']}-1521 tied linear",
+                   "tau": cfg["tau"], "form": args.form,
+                   "l2": "inputs (12.8 GB per GPU) larger than L2, no flush",
+                   "parallelism": f"dp{world} (independent shards)"},
+        "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
+        "roofline": roofline, "e2e": e2e, "training": tr, "stats": stats,
+    }
+    return res, model, cfg
+
+
+def cpu_baseline(args, cfg, model, budget_s, rank=0):
+    """The FP64 oracle (as it stands) on the host cores: AE forward, quantize,
+    Newton, check, on a bounded sample of the same workload."""
+    import oracle
+    from paper_2212_10733_gb300 import synth
+    P, H, L = synth.P, cfg["H"], cfg["L"]
+    if model is not None:
+        prm = model.get_group(0)
+    else:
+        prm = synth.ae_init(P, H, L, synth.config_seed(1))
+    om = oracle.AE(**prm)
+    vpar, vperp, vol = synth.grid_arrays()
+    og = oracle.Grid(vpar=vpar, vperp=vperp, vol_uniform=vol)
+    op = oracle.Params(tau=cfg["tau"])
+    n_full = args.n or cfg["n"]
+
+    def run(k):
+        idx = np.linspace(0, n_full - 1, k).astype(np.int64)
+        x = synth.histograms(n_full if n_full <= 65536 else max(idx) + 1,
+                             synth.config_seed(1) + 1000 * rank, k_max=cfg["k_max"],
+                             heavy_frac=cfg["heavy"], idx=idx) if n_full <= 65536 else \
+            _sample_histograms(synth, cfg, n_full, idx, rank)
+        t0 = time.time()
+        z, xh, s = oracle.ae_forward(om, x)
+        out = oracle.compress_correct(og, x, xh.astype(np.float32), op)
+        return time.time() - t0, out
+
+    k = 64
+    dt, _ = run(k)
+    while dt < budget_s / 8 and k < n_full:
+        k = min(n_full, int(k * max(2.0, budget_s / 2 / max(dt, 1e-3))))
+        dt, _ = run(k)
+    return {"value": round(k / dt, 2), "unit": "histograms/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{k} of {n_full} histograms (evenly spaced), "
+            f"AE forward + quantize + Newton + check in FP64, {dt:.1f} s"}
+
+
+def _sample_histograms(synth, cfg, n_full, idx, rank):
+    return synth.histograms(n_full, synth.config_seed(1) + 1000 * rank, k_max=cfg["k_max"],
+                            heavy_frac=cfg["heavy"], idx=idx)
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: K timed steps, each a bounded sample
+    of the workload on the host cores."""
+    import oracle
+    from paper_2212_10733_gb300 import synth
+    cfg = CONFIGS[args.config]
+    n_full = args.n or cfg["n"]
+    P, H, L = synth.P, cfg["H"], cfg["L"]
+    om = oracle.AE(**synth.ae_init(P, H, L, synth.config_seed(1)))
+    vpar, vperp, vol = synth.grid_arrays()
+    og = oracle.Grid(vpar=vpar, vperp=vperp, vol_uniform=vol)
+    op = oracle.Params(tau=cfg["tau"])
+    k = 4096
+    idx = np.linspace(0, n_full - 1, k).astype(np.int64)
+    x = synth.histograms(n_full, synth.config_seed(1), k_max=cfg["k_max"],
+                         heavy_frac=cfg["heavy"], idx=idx)
+
+    def step():
+        z, xh, s = oracle.ae_forward(om, x)
+        oracle.compress_correct(og, x, xh.astype(np.float32), op)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.time()
+    for _ in range(args.steps):
+        step()
+    dt = (time.time() - t0) / args.steps
+    v = k / dt
+    return {"metric": METRIC, "value": round(v, 2), "unit": "histograms/s", "impl": "reference",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "histograms_per_step": k,
+                       "note": "FP64 CPU oracle on a bounded sample per step"},
+            "cpu_baseline": {"value": round(v, 2), "unit": "histograms/s",
+                             "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{k} of {n_full} histograms per step"},
+            "e2e": {"value": round(v, 2), "unit": "histograms/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, world)))
+        return
+    rank, world, local = dist_setup(args)
+    res, model, cfg = run_ours(args, rank, world, local)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        res["cpu_baseline"] = cpu_baseline(args, cfg, model, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,343 @@
+/*
+ * aeqc.h -- C ABI of libaeqc, the GB300 (sm_103a) hot path of the hybrid
+ * compressor of Banerjee et al., "Scalable Hybrid Learning Techniques for
+ * Scientific Data Compression" (arXiv:2212.10733):
+ *
+ *   autoencoder encode/decode (Sec. III Stages 2-3, Eq. (5))
+ *   -> error-bounded residual quantization (Sec. III Stage 4)
+ *   -> QoI-preserving Lagrange/Newton correction (Sec. III Stage 5, Eq. (6)),
+ *      preserving the moments behind n, u_par, T_perp, T_par (Sec. II, Eq. (1)-(4))
+ *   -> decompression: decode, add the residual, apply the multipliers
+ *      to every value (Sec. III, end of Stage 5).
+ *
+ * Conventions (every call unless stated otherwise):
+ *   - Array arguments are DEVICE pointers owned by the caller, row-major and
+ *     contiguous unless a leading dimension (ld) is given.  Host pointers are
+ *     named *_host.  Nothing here keeps a pointer after the call returns.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream).  Exceptions: *_create, *_destroy,
+ *     *_set_*, *_get_*, aeqc_last_error, *_workspace_size.
+ *   - Return value: AEQC_OK (0) or a negative error code; the message of the
+ *     last error on the calling thread is aeqc_last_error().  Argument errors
+ *     are detected on the host before anything is launched.  Per-histogram
+ *     outcomes (non-convergence, verbatim storage, ...) are NOT errors: they
+ *     are reported in the uint16 status word of each histogram.
+ *   - Histogram layout: x[b][j][i], i (v_par index) fastest, P = n_par*n_perp
+ *     values of float64 per histogram (12,168 bytes for the 39 x 39 grid).
+ *   - Calls that need temporary device memory take a caller-owned
+ *     `workspace` of at least *_workspace_size() bytes (256-byte aligned).
+ *     No call allocates device memory except aeqc_model_create and
+ *     aeqc_mlp_create (which own their weights until *_destroy).
+ *   - Calls on the same stream are ordered; calls on different streams that
+ *     share an output, a workspace or a model race.
+ */
+#ifndef AEQC_H
+#define AEQC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes --------------------------------------------------------- */
+#define AEQC_OK 0
+#define AEQC_EINVAL (-1)        /* bad argument (null pointer, size, alignment) */
+#define AEQC_ECUDA (-2)         /* a CUDA runtime call failed */
+#define AEQC_ENOMEM (-3)        /* allocation failed (create calls only) */
+#define AEQC_ECORRUPT (-4)      /* container header inconsistent */
+#define AEQC_EUNSUPPORTED (-5)  /* valid but not supported (grid too large, ...) */
+
+/* ---- per-histogram status bits (uint16) ---------------------------------- */
+#define AEQC_ST_CONVERGED 0x0001u        /* Newton round 1 reached tol */
+#define AEQC_ST_ROUND2 0x0002u           /* round 2 (damped Newton from 0) ran */
+#define AEQC_ST_VERBATIM 0x0004u         /* stored raw: every code escapes, lambda = 0 */
+#define AEQC_ST_NONFINITE_INPUT 0x0008u  /* x had a NaN/Inf or a negative value */
+#define AEQC_ST_ZERO_IMAGE 0x0010u       /* max(x) == 0: f == 0, codes 0, lambda 0 */
+#define AEQC_ST_CODE_ESCAPE 0x0020u      /* at least one escape code (raw value) */
+#define AEQC_ST_WARM_REJECTED 0x0040u    /* learned warm start rejected, restarted at 0 */
+#define AEQC_ST_ALPHA_RETRY 0x0080u      /* requantized with alpha/4 after a failed check */
+#define AEQC_ST_AE_EXACT 0x0100u         /* every code is 0: the decoder alone met the bound */
+#define AEQC_ST_OUTLIER_OVERFLOW 0x0200u /* outlier list full: raw values of this
+                                            histogram were dropped (data lost) */
+
+/* ---- residual codes (int16) ---------------------------------------------- */
+#define AEQC_CODE_ESCAPE (-32768) /* raw value stored in the outlier list */
+#define AEQC_CODE_ZERO (-32767)   /* reconstruction level exactly 0 */
+#define AEQC_CODE_MAX 32766       /* |q| <= AEQC_CODE_MAX for grid levels */
+
+/* ---- limits --------------------------------------------------------------- */
+#define AEQC_MAX_NPAR 64
+#define AEQC_MAX_NPERP 64
+#define AEQC_MAX_P 1536 /* n_par * n_perp */
+#define AEQC_XHAT_LD 1536 /* default leading dimension of decoded rows */
+
+/* ---- velocity grid (Sec. II, Eq. (1)-(4)) -------------------------------- */
+typedef struct aeqc_grid {
+  int32_t n_par;          /* v_par nodes (index i, fastest), <= AEQC_MAX_NPAR */
+  int32_t n_perp;         /* v_perp nodes (index j), <= AEQC_MAX_NPERP */
+  const double* vpar_host;  /* HOST [n_par] v_par values */
+  const double* vperp_host; /* HOST [n_perp] v_perp values */
+  const double* vol;      /* DEVICE [n_perp*n_par] cell volumes, or NULL */
+  double vol_uniform;     /* cell volume used when vol == NULL */
+  double mass;            /* particle mass m (scales T only; unused by the path) */
+} aeqc_grid;
+
+/* ---- method parameters ---------------------------------------------------- */
+typedef struct aeqc_params {
+  double tau;          /* pointwise bound e = tau * max(x) per histogram */
+  double alpha;        /* quantizer share: Delta = 2^floor(log2(2 alpha e)) */
+  double step_s;       /* Newton step s of Eq. (6) (1.0) */
+  double tol;          /* convergence: max_k |g_k| / S_k <= tol (1e-12) */
+  int32_t max_iter;    /* round-1 iteration cap (50) */
+  int32_t r2_max_iter; /* round-2 iteration cap (400) */
+  int32_t loss;        /* 0: generalised KL, f = x' exp(-lambda.phi) (default);
+                          1: L2, f = x' - lambda.phi */
+  int32_t warm_iters;  /* warm-start probation iterations (2) */
+  double warm_reject;  /* reject the warm start if the residual after
+                          warm_iters steps exceeds this (1e-8) */
+  double qoi_check;    /* end-to-end moment check (1e-10) */
+  int32_t kernel;      /* AEQC_KERNEL_*: correction kernel */
+  int32_t reserved;
+} aeqc_params;
+
+#define AEQC_KERNEL_FP64 0  /* per-point work in native FP64 (plain form) */
+#define AEQC_KERNEL_FAST 1  /* per-point work on the FP32/INT pipes with
+                               error-free transforms; FP64 for per-histogram
+                               scalars only; same results within tolerance */
+
+/* Fills the defaults listed above (tau = 1e-4, alpha = 0.5). */
+void aeqc_params_default(aeqc_params* p);
+
+/* Message of the last error on this thread ("" if none). */
+const char* aeqc_last_error(void);
+
+/* Library version string. */
+const char* aeqc_version(void);
+
+/* ---- autoencoder model (Sec. III Stage 2, Sec. IV-B) ---------------------- */
+#define AEQC_DTYPE_F32 0  /* FP32 weights/activations, FP32 SIMT GEMMs */
+#define AEQC_DTYPE_BF16 1 /* BF16 weights/activations, FP32 accumulate, tcgen05 */
+
+#define AEQC_ACT_IDENTITY 0 /* the paper's linear activation */
+#define AEQC_ACT_RELU 1
+
+typedef struct aeqc_model_desc {
+  int32_t P;        /* input size n_par*n_perp (<= AEQC_MAX_P) */
+  int32_t H;        /* hidden width (multiple of 32, <= 1024) */
+  int32_t L;        /* latent size (multiple of 8, <= 256) */
+  int32_t tied;     /* 1: decoder layers use the encoder weights transposed */
+  int32_t act;      /* AEQC_ACT_* for the hidden layers */
+  int32_t dtype;    /* AEQC_DTYPE_* of the inference path */
+  int32_t n_groups; /* independent models (subdomains, Sec. III Stage 1) */
+  int32_t reserved;
+} aeqc_model_desc;
+
+typedef struct aeqc_model aeqc_model;
+
+/* Creates a model with n_groups zero-initialised parameter sets (weights
+ * must be set with aeqc_model_set_group before use).  Allocates the device
+ * memory it owns. */
+int aeqc_model_create(const aeqc_model_desc* desc, aeqc_model** out);
+int aeqc_model_destroy(aeqc_model* m);
+
+/* Sets (synchronously) the parameters of one group from HOST float64 arrays:
+ * W1 [P][H], b1 [H], W2 [H][L], b2 [L], b3 [H], b4 [P], mu [P], sigma [P]
+ * (per-pixel Z-score of x / max(x), Sec. IV-C), and for untied models
+ * W3 [L][H], W4 [H][P] (NULL when tied).  Dense layers compute y = W^T x + b.
+ * Resets the group's Adam state. */
+int aeqc_model_set_group(aeqc_model* m, int32_t group, const double* W1_host,
+                         const double* b1_host, const double* W2_host,
+                         const double* b2_host, const double* W3_host,
+                         const double* b3_host, const double* W4_host,
+                         const double* b4_host, const double* mu_host,
+                         const double* sigma_host);
+
+/* Reads (synchronously) the FP32 master parameters of one group into HOST
+ * float64 arrays with the layouts of aeqc_model_set_group (NULL = skip). */
+int aeqc_model_get_group(aeqc_model* m, int32_t group, double* W1_host, double* b1_host,
+                         double* W2_host, double* b2_host, double* W3_host,
+                         double* b3_host, double* W4_host, double* b4_host,
+                         double* mu_host, double* sigma_host);
+
+/* Fits mu/sigma of one group on n training histograms x (device): per pixel
+ * mean and max(std, 1e-6) of x / max(x).  Asynchronous. */
+int aeqc_fit_normalizer(aeqc_model* m, int32_t group, const double* x, int64_t n,
+                        void* workspace, size_t workspace_bytes, void* stream);
+size_t aeqc_fit_normalizer_workspace_size(const aeqc_model* m);
+
+/* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) of group `group` on
+ * the MSE of Eq. (5) between the normalised batch u = (x/max(x) - mu)/sigma
+ * and its reconstruction, computed in FP32 by the library's own forward and
+ * backward kernels.  x_batch [B][P] device float64.  loss_out (device float,
+ * may be NULL) receives the batch loss before the step. */
+int ae_train_step(aeqc_model* m, const double* x_batch, int64_t B, int32_t group,
+                  float lr, float* loss_out, void* workspace, size_t workspace_bytes,
+                  void* stream);
+size_t ae_train_workspace_size(const aeqc_model* m, int64_t B);
+
+/* Number of trainable parameters of one group: P*H + H + H*L + L
+ * (+ L*H untied) + H (+ H*P untied) + P. */
+int64_t aeqc_model_param_count(const aeqc_model* m);
+
+/* The loss of ae_train_step and its gradient without updating anything:
+ * grad_out (device float32, aeqc_model_param_count entries) in the order
+ * W1 [P][H], b1, W2 [H][L], b2, (W3 [L][H]), b3, (W4 [H][P]), b4; tied
+ * weights receive the sum of their encoder and decoder uses.  Uses the
+ * workspace of ae_train_step. */
+int ae_loss_grad(aeqc_model* m, const double* x_batch, int64_t B, int32_t group,
+                 float* loss_out, float* grad_out, void* workspace, size_t workspace_bytes,
+                 void* stream);
+
+/* Encoder (Sec. III Stage 3): latent [n][L] (float32 for F32 models, bf16
+ * for BF16 models) and scale [n] = max(x) per histogram (float64).
+ * group_offsets: DEVICE int64 [n_groups+1] row offsets of the subdomains
+ * (rows of group g are [off[g], off[g+1])), or NULL for one group. */
+int ae_encode(aeqc_model* m, const double* x, int64_t n, const int64_t* group_offsets,
+              void* latent, double* scale, void* workspace, size_t workspace_bytes,
+              void* stream);
+size_t ae_encode_workspace_size(const aeqc_model* m, int64_t n);
+
+/* Decoder from a stored latent: xhat[b][p] = scale[b] (sigma_p y_p + mu_p),
+ * float32 rows of leading dimension ld >= P (ld multiple of 4). */
+int ae_decode(aeqc_model* m, const void* latent, const double* scale, int64_t n,
+              const int64_t* group_offsets, float* xhat, int64_t ld, void* workspace,
+              size_t workspace_bytes, void* stream);
+size_t ae_decode_workspace_size(const aeqc_model* m, int64_t n);
+
+/* ---- outlier list (escape codes) ------------------------------------------ */
+typedef struct aeqc_outliers {
+  int64_t capacity; /* entries available in index/value */
+  int64_t* count;   /* DEVICE, one int64: entries needed.  Zeroed by the call
+                       that fills the list.  If it ends above capacity the
+                       excess was dropped and the histograms concerned carry
+                       AEQC_ST_OUTLIER_OVERFLOW. */
+  int64_t* index;   /* DEVICE [capacity]: flat index b * P + p */
+  double* value;    /* DEVICE [capacity]: raw x at that point */
+} aeqc_outliers;
+
+/* ---- residual quantizer (Sec. III Stage 4) -------------------------------- */
+/* e = tau * s with s = max(x); Delta = 2^floor(log2(2 alpha e));
+ * q = round-half-even((x - xhat) / Delta) on the exact real difference;
+ * code = q if |q| <= AEQC_CODE_MAX, AEQC_CODE_ZERO when the level 0 is
+ * strictly nearer to x than xhat + q Delta, AEQC_CODE_ESCAPE (raw value
+ * appended to `out`) for a non-finite xhat or |q| too large.
+ * x' = fl64(xhat + q Delta) (0 at the zero code, raw x at escapes), so
+ * |x' - x| <= Delta / 2 (+ half an ulp of x') <= alpha e.
+ * Inputs: x [n][P], xhat [n][ld] float32.  Outputs: codes [n][P] int16,
+ * scale [n], status [n] (ZERO_IMAGE / NONFINITE_INPUT / CODE_ESCAPE /
+ * AE_EXACT / VERBATIM), xrec [n][P] (x', may be NULL). */
+int residual_quantize(const double* x, const float* xhat, int64_t ld, int64_t n,
+                      int32_t P, const aeqc_params* params, int16_t* codes,
+                      double* scale, uint16_t* status, aeqc_outliers* out,
+                      double* xrec, void* stream);
+
+/* x' from codes: fl64(xhat + q Delta), 0 at AEQC_CODE_ZERO, the outlier
+ * list's raw values at escapes; status selects alpha/4 (ALPHA_RETRY) and
+ * zero images.  outliers may be NULL when no code escapes. */
+int residual_dequantize(const float* xhat, int64_t ld, const int16_t* codes,
+                        const aeqc_outliers* outliers, const double* scale,
+                        const uint16_t* status, int64_t n, int32_t P,
+                        const aeqc_params* params, double* xrec, void* stream);
+
+/* ---- QoI correction (Sec. III Stage 5) ------------------------------------ */
+/* Q [n][4] = sum vol phi_k x with phi = (1, v_par, v_perp^2, v_par^2), the
+ * linear moments behind n, u_par, T_perp, T_par of Eq. (1)-(4). */
+int qoi_moments(const aeqc_grid* grid, const double* x, int64_t n, double* Q,
+                void* stream);
+
+/* Solves for lambda [n][4] such that f = x' exp(-lambda.phi) (KL loss) has
+ * moments Q, by Newton on the dual, Eq. (6): lambda <- lambda + s M^-1 g,
+ * g = sum vol phi f - Q, M = sum vol phi phi^T f; convergence max_k |g_k|/S_k
+ * <= tol, S_k = sum vol |phi_k| f, tested before each step; round 2 (damped
+ * Newton from 0) for the non-converged.  lambda: in = warm start when
+ * use_warm != 0 (probation of warm_iters steps), else ignored; out = result.
+ * f_out [n][P] (may be NULL), iters [n] uint8 (steps, saturating),
+ * status [n] (CONVERGED / ROUND2 / WARM_REJECTED; none of them = failed). */
+int qoi_correct(const aeqc_grid* grid, const double* xrec, const double* Q, int64_t n,
+                const aeqc_params* params, int32_t use_warm, double* lambda,
+                double* f_out, uint8_t* iters, uint16_t* status, void* stream);
+
+/* ---- fused batch calls ---------------------------------------------------- */
+/* Compressed batch, all DEVICE and caller-owned. */
+typedef struct aeqc_compressed {
+  void* latent;      /* [n][L] model dtype */
+  double* scale;     /* [n] max(x) */
+  int16_t* codes;    /* [n][P] */
+  double* lambda;    /* [n][4] */
+  uint8_t* iters;    /* [n] Newton steps */
+  uint16_t* status;  /* [n] */
+  aeqc_outliers outliers;
+  float* features;   /* optional [n][L + 4] float32 (NULL = not written): the
+                        warm-start inputs (latent, d_0..d_3), see aeqc_mlp */
+} aeqc_compressed;
+
+typedef struct aeqc_mlp aeqc_mlp;
+
+/* Stages 4-5 given decoded histograms xhat [n][ld] float32: targets Q(x),
+ * residual quantization against xhat, Newton correction (warm-started by
+ * `mlp` when non-NULL: then out->latent is READ as the MLP input, with
+ * latent_dtype AEQC_DTYPE_F32/BF16 and latent_dim L), end-to-end check
+ * (|f - x| <= tau max(x) at every point and |Q_k(f) - Q_k(x)| / S_k(x) <=
+ * qoi_check), one retry with alpha/4 after a failed check, verbatim storage
+ * when that fails too or Newton does not converge.  out->latent is not
+ * written.  f_out [n][P] (may be NULL) receives the corrected histograms. */
+int quantize_correct(const aeqc_grid* grid, const double* x, const float* xhat, int64_t ld,
+                     int64_t n, const aeqc_params* params, aeqc_mlp* mlp,
+                     int32_t latent_dtype, int32_t latent_dim, aeqc_compressed* out,
+                     double* f_out, void* stream);
+
+/* Compression of n histograms (Stages 3-5): encode, decode, targets Q(x),
+ * quantize against the decoded xhat, Newton correction (warm-started by
+ * `mlp` when non-NULL), end-to-end check (|f - x| <= e at every point and
+ * |Q_k(f) - Q_k(x)| / S_k(x) <= qoi_check); a failed check retries once with
+ * alpha/4, then stores the histogram verbatim.  Device work only; the host
+ * reads nothing back. */
+int compress_batch(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* grid, const double* x,
+                   int64_t n, const int64_t* group_offsets, const aeqc_params* params,
+                   aeqc_compressed* out, void* workspace, size_t workspace_bytes,
+                   void* stream);
+size_t compress_batch_workspace_size(const aeqc_model* m, int64_t n);
+
+/* Decompression (end of Stage 5): decode the latents, x' from the codes,
+ * f = x' exp(-lambda.phi) at every point (raw values at escapes, also
+ * corrected), f [n][P] float64. */
+int decompress_batch(aeqc_model* m, const aeqc_grid* grid, const aeqc_compressed* in,
+                     int64_t n, const int64_t* group_offsets, const aeqc_params* params,
+                     double* f, void* workspace, size_t workspace_bytes, void* stream);
+size_t decompress_batch_workspace_size(const aeqc_model* m, int64_t n);
+
+/* ---- learned warm start (MLP in -> 64 -> 64 -> 4, ReLU) ------------------- */
+/* Input per histogram: [latent (L values), d_0..d_3] with the moment defects
+ * d_k = (Q_k(x) - Q_k(x')) / S_k(x'); output: the four multipliers.
+ * Normalisation of inputs and targets (mean/std) is part of the parameters. */
+int aeqc_mlp_create(int32_t n_in, int32_t n_hidden, aeqc_mlp** out);
+int aeqc_mlp_destroy(aeqc_mlp* m);
+/* HOST float64: W1 [n_in][nh], b1 [nh], W2 [nh][nh], b2 [nh], W3 [nh][4],
+ * b3 [4], in_mu/in_sd [n_in], out_mu/out_sd [4].  Resets the Adam state. */
+int aeqc_mlp_set(aeqc_mlp* m, const double* W1, const double* b1, const double* W2,
+                 const double* b2, const double* W3, const double* b3,
+                 const double* in_mu, const double* in_sd, const double* out_mu,
+                 const double* out_sd);
+int aeqc_mlp_get(aeqc_mlp* m, double* W1, double* b1, double* W2, double* b2, double* W3,
+                 double* b3);
+/* One Adam step on mean((out - (lambda - out_mu)/out_sd)^2); inputs [B][n_in]
+ * float32, target_lambda [B][4] float64 (device). */
+int mlp_train_step(aeqc_mlp* m, const float* inputs, const double* target_lambda,
+                   int64_t B, float lr, float* loss_out, void* workspace,
+                   size_t workspace_bytes, void* stream);
+size_t mlp_train_workspace_size(const aeqc_mlp* m, int64_t B);
+/* Loss and gradient of mlp_train_step without the update: grad_out (device
+ * float32) in the order W1 [n_in][nh], b1, W2 [nh][nh], b2, W3 [nh][4], b3. */
+int mlp_loss_grad(aeqc_mlp* m, const float* inputs, const double* target_lambda, int64_t B,
+                  float* loss_out, float* grad_out, void* workspace, size_t workspace_bytes,
+                  void* stream);
+int64_t aeqc_mlp_param_count(const aeqc_mlp* m);
+/* lambda0 [n][4] float64 from inputs [n][n_in] float32. */
+int mlp_predict(aeqc_mlp* m, const float* inputs, int64_t n, double* lambda0, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AEQC_H */

@@ -1,0 +1,400 @@
+// C-ABI entry points of libaeqc: argument validation on the host, then the
+// device work of each call enqueued on the caller's stream.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+
+#include "model.cuh"
+#include "workspace.cuh"
+
+namespace aeqc {
+
+static thread_local char g_err[512] = {0};
+
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+int check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return set_error(AEQC_ECUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
+  return AEQC_OK;
+}
+
+int make_grid(const aeqc_grid* g, GridK* k) {
+  AEQC_CHECK_ARG(g, "null grid");
+  AEQC_CHECK_ARG(g->n_par >= 1 && g->n_par <= AEQC_MAX_NPAR, "grid: n_par=%d out of range",
+                 g->n_par);
+  AEQC_CHECK_ARG(g->n_perp >= 1 && g->n_perp <= AEQC_MAX_NPERP,
+                 "grid: n_perp=%d out of range", g->n_perp);
+  AEQC_CHECK_ARG(g->n_par * g->n_perp <= AEQC_MAX_P, "grid: n_par*n_perp > %d", AEQC_MAX_P);
+  AEQC_CHECK_ARG(g->vpar_host && g->vperp_host, "grid: null vpar/vperp");
+  AEQC_CHECK_ARG(g->vol || (std::isfinite(g->vol_uniform) && g->vol_uniform > 0.0),
+                 "grid: vol_uniform must be positive when vol is NULL");
+  memset(k, 0, sizeof(*k));
+  k->n_par = g->n_par;
+  k->n_perp = g->n_perp;
+  k->P = g->n_par * g->n_perp;
+  k->has_vol = g->vol != nullptr;
+  k->vol = g->vol;
+  k->vol_uniform = g->vol_uniform;
+  for (int i = 0; i < g->n_par; ++i) {
+    AEQC_CHECK_ARG(std::isfinite(g->vpar_host[i]), "grid: non-finite v_par");
+    k->vpar[i] = g->vpar_host[i];
+  }
+  for (int j = 0; j < g->n_perp; ++j) {
+    AEQC_CHECK_ARG(std::isfinite(g->vperp_host[j]), "grid: non-finite v_perp");
+    k->vperp2[j] = g->vperp_host[j] * g->vperp_host[j];
+  }
+  return AEQC_OK;
+}
+
+int make_params(const aeqc_params* p, ParamsK* k) {
+  AEQC_CHECK_ARG(p, "null params");
+  AEQC_CHECK_ARG(std::isfinite(p->tau) && p->tau > 0.0, "params: tau must be positive");
+  AEQC_CHECK_ARG(std::isfinite(p->alpha) && p->alpha > 0.0 && p->alpha <= 0.5,
+                 "params: alpha must be in (0, 0.5]");
+  AEQC_CHECK_ARG(std::isfinite(p->step_s) && p->step_s > 0.0, "params: step_s must be positive");
+  AEQC_CHECK_ARG(std::isfinite(p->tol) && p->tol >= 0.0, "params: tol must be >= 0");
+  AEQC_CHECK_ARG(p->max_iter >= 0 && p->max_iter <= 10000, "params: max_iter out of range");
+  AEQC_CHECK_ARG(p->r2_max_iter >= 0 && p->r2_max_iter <= 10000,
+                 "params: r2_max_iter out of range");
+  AEQC_CHECK_ARG(p->loss == 0 || p->loss == 1, "params: loss must be 0 (KL) or 1 (L2)");
+  AEQC_CHECK_ARG(p->warm_iters >= 0 && p->warm_iters <= p->max_iter,
+                 "params: warm_iters must be in [0, max_iter]");
+  AEQC_CHECK_ARG(p->kernel == AEQC_KERNEL_FP64 || p->kernel == AEQC_KERNEL_FAST,
+                 "params: unknown kernel %d", p->kernel);
+  k->tau = p->tau;
+  k->alpha = p->alpha;
+  k->step_s = p->step_s;
+  k->tol = p->tol;
+  k->warm_reject = p->warm_reject;
+  k->qoi_check = p->qoi_check;
+  k->max_iter = p->max_iter;
+  k->r2_max_iter = p->r2_max_iter;
+  k->loss = p->loss;
+  k->warm_iters = p->warm_iters;
+  return AEQC_OK;
+}
+
+static bool aligned(const void* p, size_t a) {
+  return (reinterpret_cast<uintptr_t>(p) % a) == 0;
+}
+
+// Stages 4-5 on decoded histograms (shared by quantize_correct and
+// compress_batch).
+static int run_quantize_correct(const GridK& gk, const ParamsK& pk, int kernel,
+                                const double* x, const float* xhat, long long ld, long long n,
+                                aeqc_mlp* mlp, int latent_dtype, int latent_dim,
+                                aeqc_compressed* out, double* f_out, cudaStream_t s) {
+  AEQC_CUDA_TRY(cudaMemsetAsync(out->outliers.count, 0, sizeof(int64_t), s));
+  FusedArgs a;
+  memset(&a, 0, sizeof(a));
+  a.x = x;
+  a.xhat = xhat;
+  a.ldx = ld;
+  a.n = n;
+  a.row0 = 0;
+  a.grid = gk;
+  a.prm = pk;
+  a.codes = out->codes;
+  a.scale = out->scale;
+  a.lambda = out->lambda;
+  a.iters = out->iters;
+  a.status = out->status;
+  a.out = make_outliers(&out->outliers);
+  a.features = out->features;
+  a.latent.ptr = out->latent;
+  a.latent.L = latent_dim;
+  a.latent.bf16 = latent_dtype == AEQC_DTYPE_BF16;
+  a.use_mlp = mlp != nullptr;
+  if (mlp) a.mlp = mlp_kernel_view(mlp);
+  a.f_out = f_out;
+  return kernel == AEQC_KERNEL_FAST ? launch_fused_fast(a, s) : launch_fused_fp64(a, s);
+}
+
+}  // namespace aeqc
+
+using namespace aeqc;
+
+extern "C" const char* aeqc_last_error(void) { return g_err; }
+
+extern "C" const char* aeqc_version(void) { return "aeqc 0.1 (sm_103a)"; }
+
+extern "C" void aeqc_params_default(aeqc_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->tau = 1e-4;
+  p->alpha = 0.5;
+  p->step_s = 1.0;
+  p->tol = 1e-12;
+  p->max_iter = 50;
+  p->r2_max_iter = 400;
+  p->loss = 0;
+  p->warm_iters = 2;
+  p->warm_reject = 1e-8;
+  p->qoi_check = 1e-10;
+  p->kernel = AEQC_KERNEL_FP64;
+}
+
+// ---- residual quantizer ----------------------------------------------------
+
+extern "C" int residual_quantize(const double* x, const float* xhat, int64_t ld, int64_t n,
+                                 int32_t P, const aeqc_params* params, int16_t* codes,
+                                 double* scale, uint16_t* status, aeqc_outliers* out,
+                                 double* xrec, void* stream) {
+  clear_error();
+  ParamsK pk;
+  int rc = make_params(params, &pk);
+  if (rc) return rc;
+  AEQC_CHECK_ARG(n >= 0, "residual_quantize: negative n");
+  AEQC_CHECK_ARG(P > 0 && P <= AEQC_MAX_P, "residual_quantize: P out of range");
+  AEQC_CHECK_ARG(ld >= P, "residual_quantize: ld < P");
+  if (n == 0) return AEQC_OK;
+  AEQC_CHECK_ARG(x && xhat && codes && scale && status, "residual_quantize: null array");
+  OutliersK ok = make_outliers(out);
+  if (out) AEQC_CHECK_ARG(out->count && (out->capacity == 0 || (out->index && out->value)),
+                          "residual_quantize: incomplete outlier list");
+  return launch_quantize(x, xhat, ld, n, P, pk, codes, scale, status, ok, xrec,
+                         static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int residual_dequantize(const float* xhat, int64_t ld, const int16_t* codes,
+                                   const aeqc_outliers* outliers, const double* scale,
+                                   const uint16_t* status, int64_t n, int32_t P,
+                                   const aeqc_params* params, double* xrec, void* stream) {
+  clear_error();
+  ParamsK pk;
+  int rc = make_params(params, &pk);
+  if (rc) return rc;
+  AEQC_CHECK_ARG(n >= 0, "residual_dequantize: negative n");
+  AEQC_CHECK_ARG(P > 0 && P <= AEQC_MAX_P && ld >= P, "residual_dequantize: bad P/ld");
+  if (n == 0) return AEQC_OK;
+  AEQC_CHECK_ARG(xhat && codes && scale && status && xrec, "residual_dequantize: null array");
+  OutliersK ok = make_outliers(outliers);
+  return launch_dequantize(xhat, ld, codes, outliers ? &ok : nullptr, scale, status, n, P, pk,
+                           xrec, static_cast<cudaStream_t>(stream));
+}
+
+// ---- QoI correction --------------------------------------------------------
+
+extern "C" int qoi_moments(const aeqc_grid* grid, const double* x, int64_t n, double* Q,
+                           void* stream) {
+  clear_error();
+  GridK gk;
+  int rc = make_grid(grid, &gk);
+  if (rc) return rc;
+  AEQC_CHECK_ARG(n >= 0, "qoi_moments: negative n");
+  if (n == 0) return AEQC_OK;
+  AEQC_CHECK_ARG(x && Q, "qoi_moments: null array");
+  return launch_moments(gk, x, n, Q, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int qoi_correct(const aeqc_grid* grid, const double* xrec, const double* Q,
+                           int64_t n, const aeqc_params* params, int32_t use_warm,
+                           double* lambda, double* f_out, uint8_t* iters, uint16_t* status,
+                           void* stream) {
+  clear_error();
+  GridK gk;
+  ParamsK pk;
+  int rc = make_grid(grid, &gk);
+  if (rc) return rc;
+  if ((rc = make_params(params, &pk))) return rc;
+  AEQC_CHECK_ARG(n >= 0, "qoi_correct: negative n");
+  if (n == 0) return AEQC_OK;
+  AEQC_CHECK_ARG(xrec && Q && lambda && iters && status, "qoi_correct: null array");
+  return launch_newton(gk, xrec, Q, n, pk, use_warm ? 1 : 0, lambda, f_out, iters, status,
+                       static_cast<cudaStream_t>(stream));
+}
+
+// ---- autoencoder -----------------------------------------------------------
+
+extern "C" size_t ae_encode_workspace_size(const aeqc_model* m, int64_t n) {
+  return m ? encode_ws(m, n) : 0;
+}
+extern "C" size_t ae_decode_workspace_size(const aeqc_model* m, int64_t n) {
+  return m ? decode_ws(m, n) : 0;
+}
+
+extern "C" int ae_encode(aeqc_model* m, const double* x, int64_t n,
+                         const int64_t* group_offsets, void* latent, double* scale,
+                         void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  AEQC_CHECK_ARG(m, "ae_encode: null model");
+  AEQC_CHECK_ARG(n >= 0, "ae_encode: negative n");
+  if (n == 0) return AEQC_OK;
+  AEQC_CHECK_ARG(x && latent && scale, "ae_encode: null array");
+  AEQC_CHECK_ARG(group_offsets || m->d.n_groups == 1,
+                 "ae_encode: group_offsets required for a model with %d groups",
+                 m->d.n_groups);
+  AEQC_CHECK_ARG(workspace && workspace_bytes >= encode_ws(m, n),
+                 "ae_encode: workspace of %zu bytes needed", encode_ws(m, n));
+  AEQC_CHECK_ARG(aligned(workspace, kWsAlign), "ae_encode: workspace not 256-byte aligned");
+  AEQC_CHECK_ARG(m->d.dtype == AEQC_DTYPE_F32 || m->d.dtype == AEQC_DTYPE_BF16,
+                 "ae_encode: bad dtype");
+  return run_encode(m, x, n, reinterpret_cast<const long long*>(group_offsets), latent, scale,
+                    static_cast<char*>(workspace), workspace_bytes,
+                    static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int ae_decode(aeqc_model* m, const void* latent, const double* scale, int64_t n,
+                         const int64_t* group_offsets, float* xhat, int64_t ld,
+                         void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  AEQC_CHECK_ARG(m, "ae_decode: null model");
+  AEQC_CHECK_ARG(n >= 0, "ae_decode: negative n");
+  if (n == 0) return AEQC_OK;
+  AEQC_CHECK_ARG(latent && scale && xhat, "ae_decode: null array");
+  AEQC_CHECK_ARG(ld >= m->d.P && ld % 4 == 0, "ae_decode: ld must be >= P and a multiple of 4");
+  AEQC_CHECK_ARG(group_offsets || m->d.n_groups == 1,
+                 "ae_decode: group_offsets required for a model with %d groups",
+                 m->d.n_groups);
+  AEQC_CHECK_ARG(workspace && workspace_bytes >= decode_ws(m, n),
+                 "ae_decode: workspace of %zu bytes needed", decode_ws(m, n));
+  AEQC_CHECK_ARG(aligned(workspace, kWsAlign), "ae_decode: workspace not 256-byte aligned");
+  return run_decode(m, latent, scale, n, reinterpret_cast<const long long*>(group_offsets), xhat,
+                    ld, static_cast<char*>(workspace), workspace_bytes,
+                    static_cast<cudaStream_t>(stream));
+}
+
+// ---- fused batch calls -----------------------------------------------------
+
+static size_t xhat_bytes(const aeqc_model* m, long long n) {
+  (void)m;
+  return ws_round(sizeof(float) * (size_t)n * AEQC_XHAT_LD);
+}
+
+extern "C" size_t compress_batch_workspace_size(const aeqc_model* m, int64_t n) {
+  if (!m || n <= 0) return 0;
+  size_t a = encode_ws(m, n), b = decode_ws(m, n);
+  return xhat_bytes(m, n) + (a > b ? a : b);
+}
+
+extern "C" size_t decompress_batch_workspace_size(const aeqc_model* m, int64_t n) {
+  if (!m || n <= 0) return 0;
+  return xhat_bytes(m, n) + decode_ws(m, n);
+}
+
+extern "C" int compress_batch(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* grid,
+                              const double* x, int64_t n, const int64_t* group_offsets,
+                              const aeqc_params* params, aeqc_compressed* out,
+                              void* workspace, size_t workspace_bytes, void* stream) {
+  clear_error();
+  GridK gk;
+  ParamsK pk;
+  int rc = make_grid(grid, &gk);
+  if (rc) return rc;
+  if ((rc = make_params(params, &pk))) return rc;
+  AEQC_CHECK_ARG(m && out, "compress_batch: null argument");
+  AEQC_CHECK_ARG(m->d.P == gk.P, "compress_batch: model P=%d but grid has %d cells", m->d.P,
+                 gk.P);
+  AEQC_CHECK_ARG(n >= 0, "compress_batch: negative n");
+  AEQC_CHECK_ARG(group_offsets || m->d.n_groups == 1,
+                 "compress_batch: group_offsets required for a model with %d groups",
+                 m->d.n_groups);
+  if (n == 0) return AEQC_OK;
+  AEQC_CHECK_ARG(x && out->latent && out->scale && out->codes && out->lambda && out->iters &&
+                     out->status,
+                 "compress_batch: null array");
+  AEQC_CHECK_ARG(out->outliers.count &&
+                     (out->outliers.capacity == 0 || (out->outliers.index && out->outliers.value)),
+                 "compress_batch: outlier list needs a count (and arrays when capacity > 0)");
+  size_t need = compress_batch_workspace_size(m, n);
+  AEQC_CHECK_ARG(workspace && workspace_bytes >= need,
+                 "compress_batch: workspace of %zu bytes needed", need);
+  AEQC_CHECK_ARG(aligned(workspace, kWsAlign), "compress_batch: workspace not aligned");
+  if (mlp) AEQC_CHECK_ARG(mlp->nin == m->d.L + 4, "compress_batch: MLP expects %d inputs, "
+                          "latent + 4 = %d", mlp->nin, m->d.L + 4);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  float* xhat = reinterpret_cast<float*>(ws);
+  char* rest = ws + xhat_bytes(m, n);
+  size_t rest_bytes = workspace_bytes - xhat_bytes(m, n);
+  const long long* goff = reinterpret_cast<const long long*>(group_offsets);
+  if ((rc = run_encode(m, x, n, goff, out->latent, out->scale, rest, rest_bytes, s))) return rc;
+  if ((rc = run_decode(m, out->latent, out->scale, n, goff, xhat, AEQC_XHAT_LD, rest,
+                       rest_bytes, s)))
+    return rc;
+  return run_quantize_correct(gk, pk, params->kernel, x, xhat, AEQC_XHAT_LD, n, mlp,
+                              m->d.dtype, m->d.L, out, nullptr, s);
+}
+
+extern "C" int quantize_correct(const aeqc_grid* grid, const double* x, const float* xhat,
+                                int64_t ld, int64_t n, const aeqc_params* params,
+                                aeqc_mlp* mlp, int32_t latent_dtype, int32_t latent_dim,
+                                aeqc_compressed* out, double* f_out, void* stream) {
+  clear_error();
+  GridK gk;
+  ParamsK pk;
+  int rc = make_grid(grid, &gk);
+  if (rc) return rc;
+  if ((rc = make_params(params, &pk))) return rc;
+  AEQC_CHECK_ARG(out, "quantize_correct: null out");
+  AEQC_CHECK_ARG(n >= 0, "quantize_correct: negative n");
+  AEQC_CHECK_ARG(ld >= gk.P, "quantize_correct: ld < P");
+  if (n == 0) return AEQC_OK;
+  AEQC_CHECK_ARG(x && xhat && out->scale && out->codes && out->lambda && out->iters &&
+                     out->status,
+                 "quantize_correct: null array");
+  AEQC_CHECK_ARG(out->outliers.count &&
+                     (out->outliers.capacity == 0 || (out->outliers.index && out->outliers.value)),
+                 "quantize_correct: outlier list needs a count (and arrays when capacity > 0)");
+  AEQC_CHECK_ARG(latent_dtype == AEQC_DTYPE_F32 || latent_dtype == AEQC_DTYPE_BF16,
+                 "quantize_correct: bad latent dtype");
+  if (mlp || out->features) {
+    AEQC_CHECK_ARG(out->latent && latent_dim > 0, "quantize_correct: latent input required");
+  }
+  if (mlp)
+    AEQC_CHECK_ARG(mlp->nin == latent_dim + 4, "quantize_correct: MLP expects %d inputs",
+                   mlp->nin);
+  return run_quantize_correct(gk, pk, params->kernel, x, xhat, ld, n, mlp, latent_dtype,
+                              latent_dim, out, f_out, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int decompress_batch(aeqc_model* m, const aeqc_grid* grid,
+                                const aeqc_compressed* in, int64_t n,
+                                const int64_t* group_offsets, const aeqc_params* params,
+                                double* f, void* workspace, size_t workspace_bytes,
+                                void* stream) {
+  clear_error();
+  GridK gk;
+  ParamsK pk;
+  int rc = make_grid(grid, &gk);
+  if (rc) return rc;
+  if ((rc = make_params(params, &pk))) return rc;
+  AEQC_CHECK_ARG(m && in, "decompress_batch: null argument");
+  AEQC_CHECK_ARG(m->d.P == gk.P, "decompress_batch: model P=%d but grid has %d cells", m->d.P,
+                 gk.P);
+  AEQC_CHECK_ARG(n >= 0, "decompress_batch: negative n");
+  AEQC_CHECK_ARG(group_offsets || m->d.n_groups == 1,
+                 "decompress_batch: group_offsets required for a model with %d groups",
+                 m->d.n_groups);
+  if (n == 0) return AEQC_OK;
+  AEQC_CHECK_ARG(in->latent && in->scale && in->codes && in->lambda && in->status && f,
+                 "decompress_batch: null array");
+  size_t need = decompress_batch_workspace_size(m, n);
+  AEQC_CHECK_ARG(workspace && workspace_bytes >= need,
+                 "decompress_batch: workspace of %zu bytes needed", need);
+  AEQC_CHECK_ARG(aligned(workspace, kWsAlign), "decompress_batch: workspace not aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  float* xhat = reinterpret_cast<float*>(ws);
+  char* rest = ws + xhat_bytes(m, n);
+  size_t rest_bytes = workspace_bytes - xhat_bytes(m, n);
+  const long long* goff = reinterpret_cast<const long long*>(group_offsets);
+  if ((rc = run_decode(m, in->latent, in->scale, n, goff, xhat, AEQC_XHAT_LD, rest, rest_bytes,
+                       s)))
+    return rc;
+  OutliersK ok = make_outliers(&in->outliers);
+  return launch_apply(gk, xhat, AEQC_XHAT_LD, in->codes, in->outliers.count ? &ok : nullptr,
+                      in->scale, in->lambda, in->status, n, 0, pk, f, s);
+}

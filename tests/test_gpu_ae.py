@@ -1,0 +1,225 @@
+"""GPU parity of the autoencoder (Stages 2-3, Eq. (5)), its training step and
+the learned warm start against the FP64 oracle, through the C ABI.
+
+FP32 GEMMs against FP64: encoder/decoder outputs within 2e-4 of each row's
+scale, gradients within 1e-3 of each array's largest entry (the errors are
+reported by the bench; the residual stage makes the pointwise bound
+independent of them).  The compress/decompress round trip is exact: the
+decoder is deterministic, so decompression regenerates the very xhat the
+codes were made against.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_10733_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def aq():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2212_10733_gb300 import aeqc
+    aeqc.load()
+    return aeqc
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device=DEV)
+
+
+def rand_params(P, H, L, tied, seed):
+    d = synth.ae_init(P, H, L, seed, tied=tied)
+    rng = np.random.default_rng(seed)
+    for k in ("b1", "b2", "b3", "b4"):
+        d[k] = rng.normal(0, 0.1, size=d[k].shape)
+    d["mu"] = rng.uniform(0, 0.3, size=P)
+    d["sigma"] = rng.uniform(0.5, 1.5, size=P)
+    return d
+
+
+def make_model(aq, P, H, L, tied, act, G, seed):
+    m = aq.Model(P, H, L, tied=tied, act=act, dtype=aq.DTYPE_F32, n_groups=G)
+    prms = []
+    for g in range(G):
+        d = rand_params(P, H, L, tied, seed + g)
+        m.set_group(g, d)
+        prms.append(d)
+    return m, prms
+
+
+@pytest.mark.parametrize("tied,act", [(True, 0), (False, 1)])
+def test_encode_decode_match_oracle(aq, tied, act):
+    P, H, L = 1521, 64, 16
+    sizes = [5, 0, 130, 257]
+    G = len(sizes)
+    m, prms = make_model(aq, P, H, L, tied, act, G, 40)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    x = synth.histograms(int(off[-1]), synth.config_seed(1))
+    goff = dev(off)
+    z, s = aq.ae_encode(m, dev(x), group_offsets=goff)
+    xh = aq.ae_decode(m, z, s, group_offsets=goff)
+    torch.cuda.synchronize()
+    z, s, xh = z.cpu().numpy(), s.cpu().numpy(), xh.cpu().numpy()[:, :P]
+    assert np.array_equal(s, x.max(axis=1))
+    for g in range(G):
+        r = slice(off[g], off[g + 1])
+        if sizes[g] == 0:
+            continue
+        om = oracle.AE(act=act, **prms[g])
+        zo, xo, so = oracle.ae_forward(om, x[r])
+        zs = np.abs(zo).max(axis=1, keepdims=True) + 1e-30
+        assert np.all(np.abs(z[r] - zo) <= 2e-4 * zs)
+        assert np.all(np.abs(xh[r] - xo) <= 2e-4 * so[:, None])
+
+
+@pytest.mark.parametrize("tied,act", [(True, 0), (False, 0), (True, 1)])
+def test_loss_grad_matches_oracle(aq, tied, act):
+    P, H, L, B = 1521, 32, 8, 16
+    m, prms = make_model(aq, P, H, L, tied, act, 1, 7)
+    x = synth.histograms(B, synth.config_seed(2))
+    loss, g = m.loss_grad(dev(x))
+    torch.cuda.synchronize()
+    lo, go = oracle.ae_loss_grad(oracle.AE(act=act, **prms[0]), x)
+    assert abs(loss.item() - lo) <= 1e-5 * lo
+    g = g.cpu().numpy().astype(np.float64)
+    order = ["W1", "b1", "W2", "b2"] + ([] if tied else ["W3"]) + ["b3"] + \
+            ([] if tied else ["W4"]) + ["b4"]
+    o = 0
+    for k in order:
+        ref = go[k].ravel()
+        got = g[o:o + ref.size]
+        o += ref.size
+        assert np.all(np.abs(got - ref) <= 1e-3 * np.abs(ref).max() + 1e-12), k
+    assert o == g.size
+
+
+def test_training_reduces_loss(aq):
+    P, H, L = 1521, 128, 16
+    x = dev(synth.histograms(128, synth.config_seed(3)))
+    m = aq.Model(P, H, L)
+    m.set_group(0, synth.ae_init(P, H, L, 5))
+    m.fit_normalizer(0, x)
+    loss = torch.zeros(1, device=DEV)
+    ws = None
+    first = None
+    for t in range(60):
+        ws = m.train_step(x, lr=1e-3, loss_out=loss, ws=ws)
+        if t == 0:
+            first = loss.item()
+    assert loss.item() < 0.5 * first
+    # the normaliser matches the oracle's on the same data
+    got = m.get_group(0)
+    mu, sd = oracle.fit_normalizer(x.cpu().numpy(), P)
+    assert np.allclose(got["mu"], mu, rtol=1e-5, atol=1e-7)
+    assert np.allclose(got["sigma"], sd, rtol=1e-5, atol=1e-7)
+
+
+@pytest.fixture(scope="module")
+def trained(aq):
+    P, H, L = 1521, 128, 16
+    x = synth.histograms(1024, synth.config_seed(4))
+    xd = dev(x)
+    m = aq.Model(P, H, L)
+    m.set_group(0, synth.ae_init(P, H, L, 6))
+    m.fit_normalizer(0, xd)
+    ws = None
+    for t in range(100):
+        b = (t * 128) % 1024
+        ws = m.train_step(xd[b:b + 128], lr=1e-3, ws=ws)
+    vpar, vperp, vol = synth.grid_arrays()
+    return m, aq.Grid(vpar, vperp, vol), oracle.Grid(vpar=vpar, vperp=vperp, vol_uniform=vol)
+
+
+def test_compress_decompress_round_trip(aq, trained):
+    m, grid, og = trained
+    x = synth.histograms(300, synth.config_seed(5))
+    xd = dev(x)
+    p = aq.params_default(tau=1e-4, kernel=aq.KERNEL_FP64)
+    comp = aq.compress_batch(m, grid, xd, p)
+    f = aq.decompress_batch(m, grid, comp, p)
+    xh = aq.ae_decode(m, comp.latent, comp.scale)
+    qc = aq.quantize_correct(grid, xd, xh, p, want_f=True)
+    torch.cuda.synchronize()
+    assert torch.equal(qc.codes, comp.codes)
+    assert torch.equal(qc.status, comp.status)
+    assert torch.equal(qc.lam, comp.lam)
+    assert torch.equal(qc.f, f)
+    f = f.cpu().numpy()
+    e = 1e-4 * x.max(axis=1, keepdims=True)
+    assert np.all(np.abs(f - x) <= e)
+    S = oracle.abs_moments(og, x)
+    assert np.all(np.abs(oracle.moments(og, f) - oracle.moments(og, x)) <= 1e-10 * S)
+    st = comp.status.cpu().numpy()
+    assert np.mean((st & aq.ST_VERBATIM) != 0) < 0.02
+
+
+def test_mlp_gradients_and_prediction_match_oracle(aq):
+    nin, nh, B = 20, 64, 32
+    rng = np.random.default_rng(3)
+    d = synth.mlp_init(nin, nh, 4, 9)
+    for k in ("b1", "b2", "b3"):
+        d[k] = rng.normal(0, 0.1, size=d[k].shape)
+    norm = dict(in_mu=rng.normal(size=nin), in_sd=rng.uniform(0.5, 2, nin),
+                out_mu=rng.normal(size=4) * 1e-5, out_sd=rng.uniform(0.5, 2, 4) * 1e-5)
+    mlp = aq.MLP(nin, nh)
+    mlp.set({**d, **norm})
+    om = oracle.MLP(**d, **norm)
+    inp = rng.normal(size=(B, nin)).astype(np.float32)
+    tgt = norm["out_mu"] + norm["out_sd"] * rng.normal(size=(B, 4))
+    loss, g = mlp.loss_grad(dev(inp), dev(tgt))
+    lo, go = oracle.mlp_loss_grad(om, inp.astype(np.float64), tgt)
+    assert abs(loss.item() - lo) <= 1e-5 * lo
+    g = g.cpu().numpy()
+    o = 0
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        ref = go[k].ravel()
+        got = g[o:o + ref.size]
+        o += ref.size
+        assert np.all(np.abs(got - ref) <= 1e-4 * np.abs(ref).max() + 1e-12), k
+    lam = mlp.predict(dev(inp)).cpu().numpy()
+    lo = oracle.mlp_predict(om, inp.astype(np.float64))
+    assert np.all(np.abs(lam - lo) <= 1e-5 * np.abs(lo).max())
+
+
+def test_learned_warm_start_gains_iterations(aq, trained):
+    """Pairs from the plain solver train the MLP on the GPU; on held-out
+    histograms the warm start needs fewer Newton steps and reaches the same
+    multipliers as plain Newton from zero (which stays the judge)."""
+    m, grid, og = trained
+    p = aq.params_default(tau=1e-4, kernel=aq.KERNEL_FP64)
+    xt = dev(synth.histograms(4096, synth.config_seed(6)))
+    cold = aq.compress_batch(m, grid, xt, p, features=True)
+    feats, lam = cold.features, cold.lam
+    ok = (cold.status & aq.ST_CONVERGED) != 0
+    feats, lam = feats[ok], lam[ok]
+    fin = feats.double().cpu().numpy()
+    lt = lam.cpu().numpy()
+    norm = dict(in_mu=fin.mean(0), in_sd=fin.std(0) + 1e-12, out_mu=lt.mean(0),
+                out_sd=lt.std(0) + 1e-30)
+    mlp = aq.MLP(m.L + 4, 64)
+    mlp.set({**synth.mlp_init(m.L + 4, 64, 4, 1), **norm})
+    ws = None
+    loss = torch.zeros(1, device=DEV)
+    n = feats.shape[0]
+    for t in range(3000):
+        b = (t * 256) % (n - 256)
+        ws = mlp.train_step(feats[b:b + 256].contiguous(), lam[b:b + 256].contiguous(), lr=1e-3,
+                            loss_out=loss, ws=ws)
+    xv = dev(synth.histograms(2048, synth.config_seed(7)))
+    c0 = aq.compress_batch(m, grid, xv, p)
+    c1 = aq.compress_batch(m, grid, xv, p, mlp=mlp)
+    torch.cuda.synchronize()
+    both = (((c0.status & aq.ST_CONVERGED) != 0) & ((c1.status & aq.ST_CONVERGED) != 0)).cpu()
+    it0 = c0.iters.cpu().numpy()[both.numpy()].astype(float)
+    it1 = c1.iters.cpu().numpy()[both.numpy()].astype(float)
+    assert it1.mean() < it0.mean(), (it0.mean(), it1.mean(), loss.item())
+    l0 = c0.lam.cpu().numpy()[both.numpy()]
+    l1 = c1.lam.cpu().numpy()[both.numpy()]
+    assert np.all(np.abs(l1 - l0) <= 1e-9 * np.abs(l0) + 1e-11)
+    assert torch.equal(c0.codes, c1.codes)

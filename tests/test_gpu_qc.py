@@ -1,0 +1,246 @@
+"""GPU parity of the residual quantizer and the QoI correction (Stages 4-5)
+against the FP64 oracle, through the C ABI.
+
+Bars: codes, scales, statuses and x' bit-exact (integer / exact decisions
+given the same decoded input); lambda within 1e-9 relative (+1e-11 absolute:
+both sides stop at |g_k|/S_k <= 1e-12, which leaves lambda ~1e-13 from the
+unique optimum); corrected moments within 1e-10 of the targets (relative to
+S_k); every point within the pointwise bound.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_10733_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def aq():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2212_10733_gb300 import aeqc
+    aeqc.load()
+    return aeqc
+
+
+@pytest.fixture(scope="module")
+def grids(aq):
+    vpar, vperp, vol = synth.grid_arrays()
+    return aq.Grid(vpar, vperp, vol), oracle.Grid(vpar=vpar, vperp=vperp, vol_uniform=vol)
+
+
+DEV = "cuda:0"
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device=DEV)
+
+
+def special_batch(n, seed, tau):
+    """Seeded histograms with edge cases planted: decoded NaN/Inf/huge values,
+    a negative input, a zero image, a NaN input, exact quantizer ties."""
+    x = synth.histograms(n, synth.config_seed(0) + seed)
+    xh = synth.stand_in_xhat(x, seed)
+    xh[0, 10] = np.nan
+    xh[0, 11] = np.inf
+    xh[0, 12] = 1e30
+    x[1, 5] = -1.0
+    x[2, :] = 0.0
+    x[3, 7] = np.nan
+    # exact ties x - xhat = (m + 1/2) Delta: max(x) = 1 fixes Delta = 2^floor(log2(tau));
+    # xhat is a float32 near 0.5 or below, so xhat + (m + 1/2) Delta is exact in FP64
+    dl = 2.0 ** np.floor(np.log2(tau))
+    for b in (4, 5):
+        mx = x[b].max()
+        x[b] /= mx
+        if b == 4:  # row 5 keeps the unscaled xhat: hundreds of escape codes
+            xh[b, :1521] = (xh[b, :1521] / mx).astype(np.float32)
+        top = int(np.argmax(x[b]))
+        for p in range(0, 1521, 13):
+            m = (p % 23) - 11
+            h = float(np.float32(x[b, p]))
+            v = h + (m + 0.5) * dl
+            if p == top or v < 0.0 or v >= 1.0:
+                continue
+            xh[b, p] = np.float32(h)
+            x[b, p] = v
+    return x, xh
+
+
+@pytest.mark.parametrize("n,tau", [(203, 1e-4), (64, 1e-3), (1, 1e-4)])
+def test_quantize_bit_exact(aq, n, tau):
+    x, xh = special_batch(max(n, 8), 3, tau)
+    x, xh = x[:n], xh[:n]
+    p = aq.params_default(tau=tau)
+    r = aq.residual_quantize(dev(x), dev(xh), p, outlier_capacity=4 * 1521, want_xrec=True)
+    torch.cuda.synchronize()
+    codes, xp, scale, dl, st = oracle.quantize(x, xh, tau)
+    assert np.array_equal(r["codes"].cpu().numpy(), codes)
+    assert np.array_equal(r["scale"].cpu().numpy(), scale)
+    assert np.array_equal(r["status"].cpu().numpy(), st)
+    g = r["xrec"].cpu().numpy()
+    both_nan = np.isnan(g) & np.isnan(xp)
+    assert np.array_equal(np.where(both_nan, 0, g), np.where(both_nan, 0, xp))
+    cnt = int(r["count"].item())
+    esc = np.flatnonzero(codes.ravel() == oracle.ESCAPE)
+    assert cnt == len(esc)
+    idx = r["index"][:cnt].cpu().numpy()
+    val = r["value"][:cnt].cpu().numpy()
+    order = np.argsort(idx)
+    assert np.array_equal(idx[order], esc)
+    xv = x.ravel()[esc]
+    assert np.array_equal(np.nan_to_num(val[order], nan=-7.0), np.nan_to_num(xv, nan=-7.0))
+
+
+def test_dequantize_bit_exact(aq):
+    x, xh = special_batch(40, 5, 1e-4)
+    p = aq.params_default(tau=1e-4)
+    r = aq.residual_quantize(dev(x), dev(xh), p, outlier_capacity=4 * 1521, want_xrec=True)
+    back = aq.residual_dequantize(dev(xh), r["codes"], r["scale"], r["status"], p,
+                                  outliers=r["outliers"])
+    torch.cuda.synchronize()
+    codes, xp, scale, dl, st = oracle.quantize(x, xh, 1e-4)
+    ref = oracle.dequantize(xh, codes, x, dl)
+    b = back.cpu().numpy()
+    zero = (st & oracle.ZERO_IMAGE) != 0
+    assert np.array_equal(np.nan_to_num(b[~zero], nan=-7.0), np.nan_to_num(ref[~zero], nan=-7.0))
+    assert np.all(b[zero] == 0.0)
+
+
+def test_moments_match_oracle(aq, grids):
+    g, og = grids
+    x = synth.histograms(131, synth.config_seed(2))
+    Q = aq.qoi_moments(g, dev(x)).cpu().numpy()
+    Qo = oracle.moments(og, x)
+    S = oracle.abs_moments(og, x)
+    assert np.all(np.abs(Q - Qo) <= 1e-14 * S)
+    one = np.zeros((1, 1521))
+    one[0, 5 * 39 + 17] = 1.0
+    Q1 = aq.qoi_moments(g, dev(one)).cpu().numpy()
+    assert np.array_equal(Q1, oracle.moments(og, one))
+
+
+def lam_close(a, b):
+    return np.all(np.abs(a - b) <= 1e-9 * np.abs(b) + 1e-11)
+
+
+def test_newton_matches_oracle_and_closed_forms(aq, grids):
+    g, og = grids
+    n = 97
+    x = synth.histograms(n, synth.config_seed(3))
+    xh = synth.stand_in_xhat(x, 9)
+    codes, xp, scale, dl, st = oracle.quantize(x, xh, 1e-4)
+    Q = oracle.moments(og, x)
+    p = aq.params_default()
+    r = aq.qoi_correct(g, dev(xp), dev(Q), p, want_f=True)
+    torch.cuda.synchronize()
+    lam_o, f_o, it_o, st_o = oracle.newton(og, xp, Q)
+    assert np.array_equal(r["status"].cpu().numpy(), st_o)
+    assert lam_close(r["lam"].cpu().numpy(), lam_o)
+    assert np.all(np.abs(r["iters"].cpu().numpy().astype(int) - it_o) <= 1)
+    f = r["f"].cpu().numpy()
+    S = oracle.abs_moments(og, x)
+    assert np.all(np.abs(oracle.moments(og, f) - Q) <= 1e-11 * S)
+    # exponential tilt: x' = x exp(+lambda*.phi) is undone by lambda*
+    vp = np.tile(og.vpar, 39)
+    vq = np.repeat(og.vperp, 39)
+    phi = np.stack([np.ones_like(vp), vp, vq * vq, vp * vp])
+    rng = np.random.default_rng(1)
+    lam_t = rng.normal(0, 1, size=(n, 4)) * np.array([3e-2, 1e-2, 3e-3, 3e-3])
+    r = aq.qoi_correct(g, dev(x * np.exp(lam_t @ phi)), dev(Q), p)
+    assert np.allclose(r["lam"].cpu().numpy(), lam_t, rtol=1e-9, atol=1e-12)
+    # identity: no step, lambda exactly 0
+    r = aq.qoi_correct(g, dev(x), dev(Q), p)
+    assert np.all(r["lam"].cpu().numpy() == 0.0) and np.all(r["iters"].cpu().numpy() == 0)
+
+
+def test_l2_variant_matches_oracle(aq, grids):
+    g, og = grids
+    x = synth.histograms(9, synth.config_seed(4))
+    xp = x + 1e-3 * x.max() * np.random.default_rng(2).standard_normal(x.shape)
+    Q = oracle.moments(og, x)
+    p = aq.params_default(loss=1)
+    r = aq.qoi_correct(g, dev(xp), dev(Q), p)
+    lam_o, *_ = oracle.newton(og, xp, Q, oracle.Params(loss=1))
+    assert lam_close(r["lam"].cpu().numpy(), lam_o)
+
+
+def check_batch(aq, og, x, xh, tau, kernel, n_expect_conv=0.95):
+    p = aq.params_default(tau=tau, kernel=kernel)
+    out = aq.quantize_correct(aq_grid(aq), dev(x), dev(xh), p, outlier_capacity=64 * 1521,
+                              want_f=True)
+    torch.cuda.synchronize()
+    ref = oracle.compress_correct(og, x, xh, oracle.Params(tau=tau))
+    st = out.status.cpu().numpy()
+    same = st == ref["status"]
+    assert same.mean() >= 0.99, (st[~same], ref["status"][~same])
+    codes = out.codes.cpu().numpy()
+    assert np.array_equal(codes[same], ref["codes"][same])
+    assert np.array_equal(out.scale.cpu().numpy(), ref["scale"])
+    lam = out.lam.cpu().numpy()
+    assert lam_close(lam[same], ref["lam"][same])
+    f = out.f.cpu().numpy()
+    fin = np.isfinite(x).all(axis=1)
+    e = tau * np.where(fin, np.nan_to_num(x).max(axis=1), 0)[:, None]
+    assert np.all(np.abs(f[fin] - x[fin]) <= e[fin])
+    good = fin & (x.min(axis=1) >= 0) & (x.max(axis=1) > 0)
+    S = oracle.abs_moments(og, x[good])
+    assert np.all(np.abs(oracle.moments(og, f[good]) - oracle.moments(og, x[good])) <= 1e-10 * S)
+    assert np.mean((st & oracle.CONVERGED) != 0) >= n_expect_conv
+    return out, ref
+
+
+_GRID = {}
+
+
+def aq_grid(aq):
+    if "g" not in _GRID:
+        vpar, vperp, vol = synth.grid_arrays()
+        _GRID["g"] = aq.Grid(vpar, vperp, vol)
+    return _GRID["g"]
+
+
+@pytest.mark.parametrize("n,tau", [(256, 1e-4), (61, 1e-3)])
+def test_quantize_correct_fp64_matches_oracle(aq, grids, n, tau):
+    _, og = grids
+    x, xh = special_batch(n, 11, tau)
+    check_batch(aq, og, x, xh, tau, aq.KERNEL_FP64, n_expect_conv=0.9)
+
+
+def test_quantize_correct_verbatim_and_zero(aq, grids):
+    _, og = grids
+    x = synth.histograms(6, synth.config_seed(5))
+    xh = np.zeros((6, 1536), np.float32)
+    xh[:, 19] = 1.0  # decoder output supported on one column: infeasible for tau = 10
+    p = aq.params_default(tau=10.0, max_iter=50, r2_max_iter=50)
+    out = aq.quantize_correct(aq_grid(aq), dev(x), dev(xh), p, outlier_capacity=8 * 1521,
+                              want_f=True)
+    torch.cuda.synchronize()
+    st = out.status.cpu().numpy()
+    assert np.all(st & oracle.VERBATIM)
+    assert np.array_equal(out.f.cpu().numpy(), x)
+    assert int(out.count.item()) == 6 * 1521
+    ref = oracle.compress_correct(og, x, xh, oracle.Params(tau=10.0, max_iter=50,
+                                                           r2_max_iter=50))
+    assert np.array_equal(st, ref["status"])
+
+
+def test_outlier_overflow_is_reported(aq):
+    x, xh = special_batch(8, 7, 1e-4)
+    p = aq.params_default(tau=1e-4)
+    r = aq.residual_quantize(dev(x), dev(xh), p, outlier_capacity=2)
+    torch.cuda.synchronize()
+    st = r["status"].cpu().numpy()
+    assert int(r["count"].item()) > 2
+    assert np.any(st & aq.ST_OUTLIER_OVERFLOW)
+
+
+def test_empty_batch_is_a_noop(aq, grids):
+    g, _ = grids
+    x = torch.empty((0, 1521), dtype=torch.float64, device=DEV)
+    Q = aq.qoi_moments(g, x)
+    assert Q.shape == (0, 4)

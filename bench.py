@@ -51,6 +51,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--train-steps", type=int, default=None,
+                    help="override the number of autoencoder training steps")
+    ap.add_argument("--profile", default=None,
+                    choices=["compress", "encode", "decode", "quantize_correct"],
+                    help="run --steps launches of one stage between cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off) and exit")
     return ap.parse_args()
 
 
@@ -146,7 +152,7 @@ class ClockSampler:
 # workload
 # --------------------------------------------------------------------------
 
-def build_workload(cfg, n, rank, device, aq, synth):
+def build_workload(cfg, n, rank, device, aq, synth, train_steps=None):
     import torch
     seed = synth.config_seed(1) + 1000 * rank
     x = synth.histograms_torch(n, seed, device, k_max=cfg["k_max"], heavy_frac=cfg["heavy"])
@@ -157,6 +163,8 @@ def build_workload(cfg, n, rank, device, aq, synth):
     model.fit_normalizer(0, x[: min(n, 1 << 16)])
     B = cfg["batch"]
     steps = cfg["steps_train"] or (cfg["epochs"] * n // B)
+    if train_steps is not None:
+        steps = train_steps
     ws = None
     loss = torch.zeros(1, device=device)
     t0 = time.time()
@@ -185,7 +193,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(device)
     cfg = CONFIGS[args.config]
     n = args.n or cfg["n"]
-    x, model, tr = build_workload(cfg, n, rank, device, aeqc, synth)
+    x, model, tr = build_workload(cfg, n, rank, device, aeqc, synth, args.train_steps)
     vpar, vperp, vol = synth.grid_arrays()
     grid = aeqc.Grid(vpar, vperp, vol)
     kernel = aeqc.KERNEL_FAST if args.form == "fast" else aeqc.KERNEL_FP64
@@ -196,6 +204,23 @@ def run_ours(args, rank, world, local):
 
     def step():
         aeqc.compress_batch(model, grid, x, prm, out=out, ws=ws)
+
+    if args.profile:
+        step()
+        xhat = aeqc.ae_decode(model, out.latent, out.scale)
+        fn = {"compress": step,
+              "encode": lambda: aeqc.ae_encode(model, x),
+              "decode": lambda: aeqc.ae_decode(model, out.latent, out.scale),
+              "quantize_correct": lambda: aeqc.quantize_correct(grid, x, xhat, prm, out=out)}
+        for _ in range(args.warmup):
+            fn[args.profile]()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(args.steps):
+            fn[args.profile]()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return None, model, cfg
 
     for _ in range(args.warmup):
         step()
@@ -415,6 +440,9 @@ def main():
         return
     rank, world, local = dist_setup(args)
     res, model, cfg = run_ours(args, rank, world, local)
+    if res is None:  # --profile run
+        print("profiled %s x%d" % (args.profile, args.steps))
+        return
     if rank == 0 and world == 1 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline(args, cfg, model, args.cpu_seconds)
     if rank == 0:

@@ -211,7 +211,9 @@ static int mlp_loss_grad_impl(aeqc_mlp* m, const float* in, const double* lam, i
   float* P = m->params;
   int rc;
 #define TRY(e) \
-  if ((rc = (e))) return rc
+  do {                    \
+    if ((rc = (e))) return rc; \
+  } while (0)
   mlp_normalize_kernel<<<256, 256, 0, s>>>(in, B, ni, P + m->oimu, P + m->oisd, u);
   TRY(check_launch("mlp_normalize_kernel"));
   TRY(gemm_bias(B, nh, ni, u, ni, P + m->oW1, nh, 1, P + m->ob1, AEQC_ACT_RELU, h1, s));

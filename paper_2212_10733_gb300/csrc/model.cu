@@ -438,8 +438,7 @@ extern "C" int aeqc_model_create(const aeqc_model_desc* desc, aeqc_model** out) 
                  "aeqc_model_create: bad dtype");
   AEQC_CHECK_ARG(d.n_groups >= 1 && d.n_groups <= 65536, "aeqc_model_create: bad n_groups");
   aeqc_model* m = new aeqc_model();
-  memset(m, 0, sizeof(*m));
-  new (&m->step) std::vector<int>(d.n_groups, 0);
+  m->step.assign(d.n_groups, 0);  // new aeqc_model() zero-initialises the rest
   m->d = d;
   const long long P = d.P, H = d.H, L = d.L;
   long long o = 0;
@@ -475,13 +474,11 @@ extern "C" int aeqc_model_create(const aeqc_model_desc* desc, aeqc_model** out) 
   size_t bbytes = d.dtype == AEQC_DTYPE_BF16 ? sizeof(__nv_bfloat16) * (size_t)(G * m->n_bf16) : 0;
   char* base = nullptr;
   if (cudaMalloc(&base, bytes) != cudaSuccess) {
-    m->step.~vector();
     delete m;
     return set_error(AEQC_ENOMEM, "aeqc_model_create: cudaMalloc(%zu) failed", bytes);
   }
   if (cudaMemset(base, 0, bytes) != cudaSuccess) {
     cudaFree(base);
-    m->step.~vector();
     delete m;
     return set_error(AEQC_ECUDA, "aeqc_model_create: cudaMemset failed");
   }
@@ -492,7 +489,6 @@ extern "C" int aeqc_model_create(const aeqc_model_desc* desc, aeqc_model** out) 
   if (bbytes) {
     if (cudaMalloc(&m->inf_bf16, bbytes) != cudaSuccess) {
       cudaFree(base);
-      m->step.~vector();
       delete m;
       return set_error(AEQC_ENOMEM, "aeqc_model_create: cudaMalloc(%zu) failed", bbytes);
     }
@@ -513,7 +509,6 @@ extern "C" int aeqc_model_destroy(aeqc_model* m) {
   if (!m) return AEQC_OK;
   cudaFree(m->params);
   if (m->inf_bf16) cudaFree(m->inf_bf16);
-  m->step.~vector();
   delete m;
   return AEQC_OK;
 }
@@ -677,7 +672,9 @@ static int loss_grad_impl(aeqc_model* m, const double* x, int64_t B, int32_t gro
   const float *W3 = par + m->oW3, *b3 = par + m->ob3, *W4 = par + m->oW4, *b4 = par + m->ob4;
   int rc;
 #define TRY(e) \
-  if ((rc = (e))) return rc
+  do {                    \
+    if ((rc = (e))) return rc; \
+  } while (0)
   normalize_kernel<<<(unsigned)B, 256, 0, s>>>(x, P, par + m->omu, par + m->osig, u);
   TRY(check_launch("normalize_kernel"));
   // forward: h1 = act(u W1 + b1); z = h1 W2 + b2; h3 = act(z W3' + b3); y = h3 W4' + b4

@@ -117,11 +117,13 @@ def test_moments_match_oracle(aq, grids):
     Q = aq.qoi_moments(g, dev(x)).cpu().numpy()
     Qo = oracle.moments(og, x)
     S = oracle.abs_moments(og, x)
-    assert np.all(np.abs(Q - Qo) <= 1e-14 * S)
+    # different summation order: |error| <= P * eps * S_k = 1521 * 1.1e-16 * S_k
+    assert np.all(np.abs(Q - Qo) <= 1.7e-13 * S)
     one = np.zeros((1, 1521))
     one[0, 5 * 39 + 17] = 1.0
     Q1 = aq.qoi_moments(g, dev(one)).cpu().numpy()
-    assert np.array_equal(Q1, oracle.moments(og, one))
+    # same cell, same phi: equal up to the association of vol * v * v
+    assert np.allclose(Q1, oracle.moments(og, one), rtol=4.5e-16, atol=0)
 
 
 def lam_close(a, b):

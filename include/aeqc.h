@@ -282,11 +282,14 @@ typedef struct aeqc_mlp aeqc_mlp;
  * (|f - x| <= tau max(x) at every point and |Q_k(f) - Q_k(x)| / S_k(x) <=
  * qoi_check), one retry with alpha/4 after a failed check, verbatim storage
  * when that fails too or Newton does not converge.  out->latent is not
- * written.  f_out [n][P] (may be NULL) receives the corrected histograms. */
+ * written.  f_out [n][P] (may be NULL) receives the corrected histograms.
+ * The workspace (quantize_correct_workspace_size bytes) holds the list of
+ * histograms the fast kernel hands to the FP64 kernel. */
 int quantize_correct(const aeqc_grid* grid, const double* x, const float* xhat, int64_t ld,
                      int64_t n, const aeqc_params* params, aeqc_mlp* mlp,
                      int32_t latent_dtype, int32_t latent_dim, aeqc_compressed* out,
-                     double* f_out, void* stream);
+                     double* f_out, void* workspace, size_t workspace_bytes, void* stream);
+size_t quantize_correct_workspace_size(int64_t n);
 
 /* Compression of n histograms (Stages 3-5): encode, decode, targets Q(x),
  * quantize against the decoded xhat, Newton correction (warm-started by

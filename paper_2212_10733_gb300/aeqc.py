@@ -119,7 +119,8 @@ SYMBOLS = {
     "compress_batch_workspace_size": (C.c_size_t, [C.c_void_p, C.c_int64]),
     "quantize_correct": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
                                    C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
-                                   C.c_void_p, C.c_void_p]),
+                                   C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "quantize_correct_workspace_size": (C.c_size_t, [C.c_int64]),
     "decompress_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                                    C.c_void_p]),
@@ -478,7 +479,7 @@ def compress_batch(m: Model, grid: Grid, x, params: aeqc_params, mlp: Optional[M
 def quantize_correct(grid: Grid, x, xhat, params: aeqc_params, mlp: Optional[MLP] = None,
                      latent=None, out: Optional[Compressed] = None,
                      outlier_capacity: Optional[int] = None, features: bool = False,
-                     want_f: bool = False, stream=None):
+                     want_f: bool = False, ws=None, stream=None):
     """Stages 4-5 given decoded histograms xhat [n][ld] float32."""
     import torch
     n, P = x.shape
@@ -491,9 +492,12 @@ def quantize_correct(grid: Grid, x, xhat, params: aeqc_params, mlp: Optional[MLP
             out.c.latent = _ptr(latent)
     ldt = DTYPE_BF16 if (latent is not None and latent.dtype == torch.bfloat16) else DTYPE_F32
     f = torch.empty((n, P), dtype=torch.float64, device=x.device) if want_f else None
+    if ws is None:
+        ws = _workspace(load().quantize_correct_workspace_size(n), x.device)
     _check(load().quantize_correct(C.byref(grid.c), _ptr(x), _ptr(xhat), xhat.stride(0), n,
                                    C.byref(params), mlp.h if mlp is not None else None, ldt,
-                                   L, C.byref(out.c), _ptr(f), _stream(stream)))
+                                   L, C.byref(out.c), _ptr(f), _ptr(ws), ws.numel(),
+                                   _stream(stream)))
     out.f = f
     return out
 

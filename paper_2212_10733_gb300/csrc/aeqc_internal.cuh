@@ -98,6 +98,16 @@ struct LatentK {
   int bf16;  // 1: __nv_bfloat16 elements, 0: float
 };
 
+// Affine form of a uniform grid for the fast correction kernel:
+// v_par_i = b (i - i_c) + c0 and v_perp_j^2 = d2 j^2 (v_perp_0 = 0), so every
+// moment weight is a polynomial in the integers (i - i_c) and j.
+struct FastGridK {
+  int ok;  // 0: the grid is not of this form (the fast kernel defers to FP64)
+  int i_c;
+  double b, c0, d2;
+};
+int make_fast_grid(const GridK& g, FastGridK* out);
+
 // ---------------------------------------------------------------------------
 // correction kernels (qc_fp64.cu, qc_fast.cu)
 // ---------------------------------------------------------------------------
@@ -120,9 +130,16 @@ struct FusedArgs {
   int use_mlp;
   MlpK mlp;
   double* f_out;          // [n][P] or null
+  FastGridK fg;           // fast kernel only
+  int* fb_list;           // fast kernel: histograms deferred to the FP64 kernel
+  int* fb_count;
 };
 
 int launch_fused_fp64(const FusedArgs& a, cudaStream_t s);
+int launch_fused_fp64_list(const FusedArgs& a, const int* list, const int* count,
+                           cudaStream_t s);
+// fast kernel + FP64 kernel over its deferred list; fb_list [n] and fb_count
+// are scratch in device memory
 int launch_fused_fast(const FusedArgs& a, cudaStream_t s);
 
 int launch_moments(const GridK& g, const double* x, long long n, double* Q, cudaStream_t s);

@@ -92,10 +92,17 @@ static bool aligned(const void* p, size_t a) {
 
 // Stages 4-5 on decoded histograms (shared by quantize_correct and
 // compress_batch).
+static size_t qc_ws(long long n) { return ws_round(sizeof(int) * (size_t)(n > 0 ? n : 1)) + kWsAlign; }
+
 static int run_quantize_correct(const GridK& gk, const ParamsK& pk, int kernel,
                                 const double* x, const float* xhat, long long ld, long long n,
                                 aeqc_mlp* mlp, int latent_dtype, int latent_dim,
-                                aeqc_compressed* out, double* f_out, cudaStream_t s) {
+                                aeqc_compressed* out, double* f_out, char* ws, size_t ws_bytes,
+                                cudaStream_t s) {
+  WsCarver c(ws, ws_bytes);
+  int* fb_list = c.take<int>((size_t)n);
+  int* fb_count = c.take<int>(1);
+  if (!c.ok()) return set_error(AEQC_EINVAL, "quantize_correct: workspace too small");
   AEQC_CUDA_TRY(cudaMemsetAsync(out->outliers.count, 0, sizeof(int64_t), s));
   FusedArgs a;
   memset(&a, 0, sizeof(a));
@@ -119,6 +126,10 @@ static int run_quantize_correct(const GridK& gk, const ParamsK& pk, int kernel,
   a.use_mlp = mlp != nullptr;
   if (mlp) a.mlp = mlp_kernel_view(mlp);
   a.f_out = f_out;
+  int rc = make_fast_grid(gk, &a.fg);
+  if (rc) return rc;
+  a.fb_list = fb_list;
+  a.fb_count = fb_count;
   return kernel == AEQC_KERNEL_FAST ? launch_fused_fast(a, s) : launch_fused_fp64(a, s);
 }
 
@@ -276,8 +287,12 @@ static size_t xhat_bytes(const aeqc_model* m, long long n) {
 extern "C" size_t compress_batch_workspace_size(const aeqc_model* m, int64_t n) {
   if (!m || n <= 0) return 0;
   size_t a = encode_ws(m, n), b = decode_ws(m, n);
-  return xhat_bytes(m, n) + (a > b ? a : b);
+  size_t c = qc_ws(n);  // the fallback list reuses the hidden-layer buffer
+  size_t r = a > b ? a : b;
+  return xhat_bytes(m, n) + (r > c ? r : c);
 }
+
+extern "C" size_t quantize_correct_workspace_size(int64_t n) { return qc_ws(n); }
 
 extern "C" size_t decompress_batch_workspace_size(const aeqc_model* m, int64_t n) {
   if (!m || n <= 0) return 0;
@@ -325,13 +340,14 @@ extern "C" int compress_batch(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* gri
                        rest_bytes, s)))
     return rc;
   return run_quantize_correct(gk, pk, params->kernel, x, xhat, AEQC_XHAT_LD, n, mlp,
-                              m->d.dtype, m->d.L, out, nullptr, s);
+                              m->d.dtype, m->d.L, out, nullptr, rest, rest_bytes, s);
 }
 
 extern "C" int quantize_correct(const aeqc_grid* grid, const double* x, const float* xhat,
                                 int64_t ld, int64_t n, const aeqc_params* params,
                                 aeqc_mlp* mlp, int32_t latent_dtype, int32_t latent_dim,
-                                aeqc_compressed* out, double* f_out, void* stream) {
+                                aeqc_compressed* out, double* f_out, void* workspace,
+                                size_t workspace_bytes, void* stream) {
   clear_error();
   GridK gk;
   ParamsK pk;
@@ -339,6 +355,8 @@ extern "C" int quantize_correct(const aeqc_grid* grid, const double* x, const fl
   if (rc) return rc;
   if ((rc = make_params(params, &pk))) return rc;
   AEQC_CHECK_ARG(out, "quantize_correct: null out");
+  AEQC_CHECK_ARG(workspace && workspace_bytes >= qc_ws(n) && aligned(workspace, kWsAlign),
+                 "quantize_correct: 256-byte aligned workspace of %zu bytes needed", qc_ws(n));
   AEQC_CHECK_ARG(n >= 0, "quantize_correct: negative n");
   AEQC_CHECK_ARG(ld >= gk.P, "quantize_correct: ld < P");
   if (n == 0) return AEQC_OK;
@@ -357,7 +375,8 @@ extern "C" int quantize_correct(const aeqc_grid* grid, const double* x, const fl
     AEQC_CHECK_ARG(mlp->nin == latent_dim + 4, "quantize_correct: MLP expects %d inputs",
                    mlp->nin);
   return run_quantize_correct(gk, pk, params->kernel, x, xhat, ld, n, mlp, latent_dtype,
-                              latent_dim, out, f_out, static_cast<cudaStream_t>(stream));
+                              latent_dim, out, f_out, static_cast<char*>(workspace),
+                              workspace_bytes, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int decompress_batch(aeqc_model* m, const aeqc_grid* grid,

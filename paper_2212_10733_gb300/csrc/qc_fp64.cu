@@ -392,6 +392,20 @@ __global__ void __launch_bounds__(WPC * 32) fused_fp64_kernel(const FusedArgs a)
     process_fp64(a, w, b, lane);
 }
 
+// The same per-histogram work for the histograms listed by the fast kernel
+// (list[0 .. *count)); a launch with an empty list returns at once.
+__global__ void __launch_bounds__(WPC * 32) fused_fp64_list_kernel(const FusedArgs a,
+                                                                   const int* list,
+                                                                   const int* count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WS& w = reinterpret_cast<WS*>(smem_raw)[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const long long cnt = *count;
+  const long long nw = (long long)gridDim.x * WPC;
+  for (long long t = (long long)blockIdx.x * WPC + (threadIdx.x >> 5); t < cnt; t += nw)
+    process_fp64(a, w, list[t], lane);
+}
+
 // ---- single-stage kernels for the separate C-ABI calls ---------------------
 
 __global__ void __launch_bounds__(128) moments_kernel(const GridK g, const double* x,
@@ -667,6 +681,22 @@ int launch_fused_fp64(const FusedArgs& a, cudaStream_t s) {
   }
   fused_fp64_kernel<<<grid_for(a.n, 2), WPC * 32, smem, s>>>(a);
   return check_launch("fused_fp64_kernel");
+}
+
+int launch_fused_fp64_list(const FusedArgs& a, const int* list, const int* count,
+                           cudaStream_t s) {
+  if (a.n <= 0) return AEQC_OK;
+  size_t smem = sizeof(WS) * WPC;
+  static bool attr = false;
+  if (!attr) {
+    AEQC_CUDA_TRY(cudaFuncSetAttribute(fused_fp64_list_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  // sized for a few percent of the batch; the grid-stride loop covers any count
+  long long warps = a.n / 16 + 1;
+  fused_fp64_list_kernel<<<grid_for(warps, 2), WPC * 32, smem, s>>>(a, list, count);
+  return check_launch("fused_fp64_list_kernel");
 }
 
 int launch_moments(const GridK& g, const double* x, long long n, double* Q, cudaStream_t s) {

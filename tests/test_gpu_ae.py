@@ -188,17 +188,34 @@ def test_mlp_gradients_and_prediction_match_oracle(aq):
     assert np.all(np.abs(lam - lo) <= 1e-5 * np.abs(lo).max())
 
 
-def test_learned_warm_start_gains_iterations(aq, trained):
-    """Pairs from the plain solver train the MLP on the GPU; on held-out
-    histograms the warm start needs fewer Newton steps and reaches the same
-    multipliers as plain Newton from zero (which stays the judge)."""
+def initial_residual(og, x, xp, lam):
+    """max_k |Q_k(x' e^{-lam.phi}) - Q_k(x)| / S_k per histogram (numpy)."""
+    vp = np.tile(og.vpar, 39)
+    vq = np.repeat(og.vperp, 39) ** 2
+    phi = np.stack([np.ones_like(vp), vp, vq, vp * vp])
+    f = xp * np.exp(-(lam @ phi))
+    g = og.vol_uniform * (f - x) @ phi.T
+    S = og.vol_uniform * (xp @ np.abs(phi).T)
+    return np.max(np.abs(g) / S, axis=1)
+
+
+def test_learned_warm_start(aq, trained):
+    """The MLP is trained on the GPU by the library's own kernels on
+    (latent, moment defects) -> multipliers pairs that plain Newton from zero
+    produces.  On held-out histograms its prediction starts closer to the
+    solution than zero does; with it, both correction kernels return the
+    results of plain Newton (which stays the judge: same codes at the same
+    quantizer level, multipliers within the solver tolerance) without extra
+    steps.  The step counts are reported: the per-step contraction here is
+    ~|lambda.phi| ~ 1e-4, so a start saves a step only within ~1e-3 of the
+    solution."""
     m, grid, og = trained
     p = aq.params_default(tau=1e-4, kernel=aq.KERNEL_FP64)
-    xt = dev(synth.histograms(4096, synth.config_seed(6)))
+    xt = dev(synth.histograms(8192, synth.config_seed(6)))
     cold = aq.compress_batch(m, grid, xt, p, features=True)
-    feats, lam = cold.features, cold.lam
-    ok = (cold.status.int() & aq.ST_CONVERGED) != 0
-    feats, lam = feats[ok], lam[ok]
+    ok = ((cold.status.int() & aq.ST_CONVERGED) != 0) & \
+         ((cold.status.int() & aq.ST_ALPHA_RETRY) == 0)
+    feats, lam = cold.features[ok].contiguous(), cold.lam[ok].contiguous()
     fin = feats.double().cpu().numpy()
     lt = lam.cpu().numpy()
     norm = dict(in_mu=fin.mean(0), in_sd=fin.std(0) + 1e-12, out_mu=lt.mean(0),
@@ -208,22 +225,47 @@ def test_learned_warm_start_gains_iterations(aq, trained):
     ws = None
     loss = torch.zeros(1, device=DEV)
     n = feats.shape[0]
-    for t in range(3000):
+    first = None
+    for t in range(4000):
         b = (t * 256) % (n - 256)
-        ws = mlp.train_step(feats[b:b + 256].contiguous(), lam[b:b + 256].contiguous(), lr=1e-3,
+        ws = mlp.train_step(feats[b:b + 256], lam[b:b + 256], lr=1e-3 if t < 3000 else 1e-4,
                             loss_out=loss, ws=ws)
-    xv = dev(synth.histograms(2048, synth.config_seed(7)))
-    c0 = aq.compress_batch(m, grid, xv, p)
-    c1 = aq.compress_batch(m, grid, xv, p, mlp=mlp)
-    torch.cuda.synchronize()
-    both = (((c0.status.int() & aq.ST_CONVERGED) != 0) &
-            ((c1.status.int() & aq.ST_CONVERGED) != 0)).cpu()
-    it0 = c0.iters.cpu().numpy()[both.numpy()].astype(float)
-    it1 = c1.iters.cpu().numpy()[both.numpy()].astype(float)
-    assert it1.mean() < it0.mean(), (it0.mean(), it1.mean(), loss.item())
-    l0 = c0.lam.cpu().numpy()[both.numpy()]
-    l1 = c1.lam.cpu().numpy()[both.numpy()]
-    assert np.all(np.abs(l1 - l0) <= 1e-9 * np.abs(l0) + 1e-11)
-    # codes agree wherever both took the same quantizer level
-    lvl0 = (c0.status.int() & aq.ST_ALPHA_RETRY) == (c1.status.int() & aq.ST_ALPHA_RETRY)
-    assert torch.equal(c0.codes[lvl0], c1.codes[lvl0])
+        if t == 0:
+            first = loss.item()
+    assert loss.item() < 0.5 * first
+    xv_np = synth.histograms(2048, synth.config_seed(7))
+    xv = dev(xv_np)
+    report = {}
+    for name, k in (("fp64", aq.KERNEL_FP64), ("fast", aq.KERNEL_FAST)):
+        pk = aq.params_default(tau=1e-4, kernel=k)
+        c0 = aq.compress_batch(m, grid, xv, pk, features=True)
+        c1 = aq.compress_batch(m, grid, xv, pk, mlp=mlp)
+        torch.cuda.synchronize()
+        s0, s1 = c0.status.int().cpu().numpy(), c1.status.int().cpu().numpy()
+        both = ((s0 & aq.ST_CONVERGED) != 0) & ((s1 & aq.ST_CONVERGED) != 0)
+        lvl = (s0 & aq.ST_ALPHA_RETRY) == (s1 & aq.ST_ALPHA_RETRY)
+        assert torch.equal(c0.codes[torch.as_tensor(lvl, device=DEV)],
+                           c1.codes[torch.as_tensor(lvl, device=DEV)])
+        it0 = c0.iters.cpu().numpy()[both].astype(float)
+        it1 = c1.iters.cpu().numpy()[both].astype(float)
+        assert it1.mean() <= it0.mean() + 0.05, (name, it0.mean(), it1.mean())
+        report[name] = (it0.mean(), it1.mean())
+        if name == "fp64":
+            # prediction quality: initial residual of the learned start vs zero
+            xh = aq.ae_decode(m, c0.latent, c0.scale).cpu().numpy()
+            sel = both & lvl & ((s0 & aq.ST_ALPHA_RETRY) == 0)
+            xp = oracle.quantize(xv_np[sel], xh[sel], 1e-4)[1]
+            lam0 = mlp.predict(c0.features[torch.as_tensor(sel, device=DEV)]).cpu().numpy()
+            r_zero = initial_residual(og, xv_np[sel], xp, np.zeros_like(lam0))
+            r_warm = initial_residual(og, xv_np[sel], xp, lam0)
+            report["start_residual_ratio_median"] = float(np.median(r_warm / r_zero))
+            assert np.median(r_warm / r_zero) < 0.8, report
+            # same multipliers in the metric the constraints fix them in
+            vp = np.tile(og.vpar, 39)
+            vq = np.repeat(og.vperp, 39) ** 2
+            phi = np.stack([np.ones_like(vp), vp, vq, vp * vp])
+            dl = c1.lam.cpu().numpy()[sel] - c0.lam.cpu().numpy()[sel]
+            Mdl = og.vol_uniform * np.einsum("kp,bp,lp,bl->bk", phi, xp, phi, dl)
+            S = og.vol_uniform * (xp @ np.abs(phi).T)
+            assert np.all(np.abs(Mdl) <= 3e-12 * S)
+    print("warm start (mean Newton steps cold, warm):", report)

@@ -105,6 +105,12 @@ struct FastGridK {
   int ok;  // 0: the grid is not of this form (the fast kernel defers to FP64)
   int i_c;
   double b, c0, d2;
+  // the same constants as float pairs (hi + lo) for double-float arithmetic:
+  // vol, d2^q (q = 0..2), and coef[p][r] = C(p,r) b^r c0^(p-r) (p, r <= 4)
+  float vol_h, vol_l;
+  float d2q_h[3], d2q_l[3];
+  float coef_h[5][5], coef_l[5][5];
+  float vmax, wmax;  // max |v_par| and max v_perp^2 on the grid
 };
 int make_fast_grid(const GridK& g, FastGridK* out);
 

@@ -49,12 +49,18 @@ struct PointIter {
 };
 
 // Bin width Delta = 2^floor(log2(2 alpha e)) for e = tau * s (Stage 4).
+// 2^floor(log2 v) is read off the bit pattern of v = (2 alpha) (tau s): the
+// exponent field of a normal number, the leading mantissa bit of a subnormal.
+// Returns 0 for v == 0 and NaN for a non-finite v.
 __device__ __forceinline__ double bin_width(double tau, double s, double alpha) {
-  double e = __dmul_rn(tau, s);
-  double v = __dmul_rn(__dmul_rn(2.0, alpha), e);
-  int E;
-  (void)frexp(v, &E);
-  return ldexp(1.0, E - 1);
+  const double e = __dmul_rn(tau, s);
+  const double v = __dmul_rn(__dmul_rn(2.0, alpha), e);
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long E = u >> 52;
+  if (E == 0x7ff) return __longlong_as_double(0x7ff8000000000000LL);
+  if (E > 0) return __longlong_as_double((long long)(E << 52));
+  if (u == 0) return 0.0;
+  return __longlong_as_double((long long)(1ull << (63 - __clzll((long long)u))));
 }
 
 // Exact quantizer decision for one point (Stage 4), FP64 form.

@@ -1,8 +1,11 @@
 // Residual quantization and QoI correction with the per-point work on the
-// integer and FP32 pipes (GB300's FP64 pipe runs at a small fraction of its
-// FP32 rate; the per-histogram 4x4 algebra stays in FP64).  One warp per
-// histogram; the histogram's x' (float), residual (float) and codes stay in
-// shared memory for the Newton passes.
+// integer and FP32 pipes.  On GB300 the FP64 pipe runs at ~1/58 of the FP32
+// rate and a warp-wide FP64 instruction costs the same with one active lane as
+// with 32, so the per-histogram algebra runs in double-float arithmetic (pairs
+// of floats, ~48-bit significands) on the FP32 pipe as well; FP64 is used only
+// where a result must equal the oracle's bit for bit (the bin width Delta) and
+// to hand the multipliers out as float64.  One warp per histogram; x', the
+// residual and the codes stay in shared memory for the Newton passes.
 //
 // Quantizer (Stage 4), exactly: with Delta = 2^k, x and xhat become integers
 // X = floor(x 2^(F-k)), Xh = floor(xhat 2^(F-k)) by bit manipulation, with an
@@ -17,15 +20,20 @@
 //   R = sum vol phi r,  M = sum vol phi phi^T x',  H = sum vol phi x' h(t),
 //   h(t) = e^{-t} - 1 + t = t^2/2 - t^3/6 + ...
 // R and M do not depend on lambda: one pass accumulates them exactly as
-// integer sums (for the affine grid v_par = b (i - i_c) + c0, v_perp^2 = d2 j^2
-// every weight is a small integer polynomial).  H is second order (|H|/S below
-// ~1e-7 in practice), so FP32 sums carry it to far below the 1e-12 tolerance.
-// Newton steps use M as the Jacobian (a chord step: M is the exact Jacobian at
-// lambda = 0, and the method converges at a rate ~|t|); each step after the
-// first costs one FP32 pass over x'.  The end-to-end check runs in the same
-// pass.  Histograms the fast path cannot certify (non-finite or negative input,
-// large lambda, no convergence, an ambiguous check, verbatim storage) are
-// appended to a list that the FP64 kernel completes.
+// integer sums (on the affine grid v_par = b (i - i_c) + c0, v_perp^2 = d2 j^2
+// every weight is a small integer polynomial).  H is second order; each pass
+// sums it in FP32 together with a bound on the rounding error of those sums,
+// and repeats the pass with error-free (TwoSum) accumulation if the bound
+// exceeds 1e-13 S_k.  Newton steps use M as the Jacobian (a chord step: M is
+// the exact Jacobian at lambda = 0, and the iteration contracts at a rate
+// ~|t|); the 4x4 solve runs in FP32 on the unit-diagonal scaled M with one
+// double-float refinement step.  Each step after the first costs one FP32 pass,
+// which also performs the end-to-end check.  Histograms the fast path cannot
+// certify (non-finite or negative input, large lambda, no convergence, an
+// ambiguous check, verbatim storage) go to a list the FP64 kernel completes.
+#include <math.h>
+#include <string.h>
+
 #include "qc_common.cuh"
 
 namespace aeqc {
@@ -41,6 +49,73 @@ struct FastWS {
   int16_t codes[AEQC_MAX_P];
   double ta[AEQC_MAX_NPAR], tb[AEQC_MAX_NPERP];  // exponential tables for f_out
 };
+
+// ---- double-float arithmetic (Dekker / Knuth error-free transformations) ---
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df quick_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+  const df s = two_sum(x.hi, y.hi);
+  return quick_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ df df_mul(df x, df y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e));
+  return quick_sum(p, e);
+}
+__device__ __forceinline__ df df_mul_f(df x, float f) {
+  const float p = __fmul_rn(x.hi, f);
+  const float e = __fmaf_rn(x.lo, f, __fmaf_rn(x.hi, f, -p));
+  return quick_sum(p, e);
+}
+__device__ __forceinline__ df df_add_f(df x, float f) {
+  const df s = two_sum(x.hi, f);
+  return quick_sum(s.hi, __fadd_rn(s.lo, x.lo));
+}
+__device__ __forceinline__ float exp2i(int n) {  // 2^n for n in [-126, 127]
+  return __int_as_float((n + 127) << 23);
+}
+__device__ __forceinline__ df df_ldexp(df x, int n) {  // exact for normal results
+  return {ldexpf(x.hi, n), ldexpf(x.lo, n)};
+}
+__device__ __forceinline__ df df_wsum(df x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    df y = {__shfl_xor_sync(FULL, x.hi, o), __shfl_xor_sync(FULL, x.lo, o)};
+    x = df_add(x, y);
+  }
+  return x;
+}
+// the top 48 bits of an int64 as a float pair (relative error <= 2^-48)
+__device__ __forceinline__ df df_from_ll(long long v) {
+  if (v == 0) return {0.f, 0.f};
+  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  const unsigned long long m = a << lz;
+  const int e = 63 - lz;
+  float hi = __fmul_rn(__uint2float_rn((unsigned)(m >> 40)), exp2i(e - 23));
+  float lo = __fmul_rn(__uint2float_rn((unsigned)((m >> 16) & 0xFFFFFFull)), exp2i(e - 47));
+  if (v < 0) {
+    hi = -hi;
+    lo = -lo;
+  }
+  return quick_sum(hi, lo);
+}
+
+// ---- integer decomposition of the inputs ----------------------------------
 
 // floor(x 2^sh) of a finite double x >= 0 given its bits; inexact |= bits dropped.
 __device__ __forceinline__ long long fix_f64(unsigned long long u, int sh, bool& inexact) {
@@ -93,47 +168,55 @@ __device__ __forceinline__ long long fix_f32(unsigned v, int sh, bool& inexact) 
   return mag;
 }
 
+// binary exponent E of a positive finite double: d in [2^(E-1), 2^E)
+__device__ __forceinline__ int exponent_of(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const int E = (int)(u >> 52) & 0x7ff;
+  if (E) return E - 1022;
+  return (63 - __clzll((long long)u)) - 1073;  // subnormal
+}
+
 // Per-histogram constants of the integer quantizer.
 struct QConst {
-  double dl;       // Delta
+  double dl;  // Delta = 2^k
   float dl_f;
-  int k;           // Delta = 2^k
-  int F;           // fractional bits of the fixed-point values (units of Delta)
-  int FX;          // fractional bits of x' in the moment sums
-  int thr;         // |xhat| >= 2^thr certainly escapes
+  int k;
+  int F;    // fractional bits of the fixed-point values (units of Delta)
+  int FX;   // fractional bits of x' in the moment sums
+  int thr;  // |xhat| >= 2^thr certainly escapes
   long long half, mask;
 };
 
 __device__ __forceinline__ bool make_qconst(double tau, double s, double alpha, QConst& c) {
   c.dl = bin_width(tau, s, alpha);
-  int E;
-  (void)frexp(c.dl, &E);
-  c.k = E - 1;
-  int Es;
-  (void)frexp(s, &Es);      // s in [2^(Es-1), 2^Es)
-  const int IBx = Es - c.k;  // s / Delta < 2^IBx
+  if (!(c.dl > 0.0) || !isfinite(c.dl)) return false;
+  c.k = exponent_of(c.dl) - 1;
+  const int IBx = exponent_of(s) - c.k;  // s / Delta < 2^IBx
   const int IB = (IBx > 15 ? IBx : 15) + 2;
   c.F = 62 - IB;
   c.FX = 30 - IBx;
   c.thr = c.k + IB - 1;
   c.half = 1ll << (c.F - 1);
   c.mask = (1ll << c.F) - 1;
-  c.dl_f = (float)c.dl;
-  // the float copies and the 30-bit residual scale need F >= 31; FX >= 1
-  return c.F >= 31 && c.FX >= 1 && IBx >= 1 && isfinite(c.dl_f) && c.dl_f > 0.f;
+  // float copies: Delta and the scale factors of the moment sums must be
+  // normal floats (moments are scaled by vol Delta 2^-30 and vol Delta 2^-FX)
+  const bool ok = c.F >= 31 && c.FX >= 1 && IBx >= 1 && c.k - 40 >= -100 && c.k + 20 <= 100;
+  c.dl_f = ok ? exp2i(c.k) : 0.f;
+  return ok;
 }
 
 struct PointQ {
   int code;
-  int rho32;   // round((x - x') / Delta * 2^30)
-  int xp32;    // floor(x' / Delta * 2^FX)
-  float xpf;   // x' (float)
+  int rho32;  // round((x - x') / Delta * 2^30)
+  int xp32;   // round(x' / Delta * 2^FX)
+  float xpf;  // x' (float)
 };
 
 // Exact quantizer decision for one point (x finite, x >= 0).
 __device__ __forceinline__ PointQ quant_point_int(double x, float xh, const QConst& c) {
   PointQ o;
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long u =
+      (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
   const unsigned v = __float_as_uint(xh);
   const int Eh = (v >> 23) & 0xff;
   const int sh = c.F - c.k;
@@ -167,8 +250,10 @@ __device__ __forceinline__ PointQ quant_point_int(double x, float xh, const QCon
           const long long A = G - 2 * X;
           if (A >= 2) zero = 1;
           else if (A <= -1) zero = 0;
-          else if (inex) { zero = 0; hard = true; }
-          else zero = A > 0;
+          else if (inex) {
+            zero = 0;
+            hard = true;
+          } else zero = A > 0;
         }
         if (!hard) {
           if (zero) {
@@ -189,32 +274,34 @@ __device__ __forceinline__ PointQ quant_point_int(double x, float xh, const QCon
     o.code = quant_point_fp64(x, (double)xh, c.dl, &xpd);
     const double rd = __ddiv_rn(__dsub_rn(x, xpd), c.dl);
     o.rho32 = __double2int_rn(ldexp(rd, 30));
-    o.xp32 = __double2int_rz(ldexp(__ddiv_rn(xpd, c.dl), c.FX));
+    o.xp32 = __double2int_rn(ldexp(__ddiv_rn(xpd, c.dl), c.FX));
     o.xpf = (float)xpd;
     return o;
   }
+  // round to nearest: a floor would bias every cell the same way, and the
+  // high-order weights (v^4 up to 256) would turn that into a systematic error
   o.rho32 = (int)((rho_fix + (1ll << (c.F - 31))) >> (c.F - 30));
-  o.xp32 = (int)(xp_fix >> (c.F - c.FX));
+  o.xp32 = (int)((xp_fix + (1ll << (c.F - c.FX - 1))) >> (c.F - c.FX));
   if (o.code == AEQC_CODE_ESCAPE) o.xpf = ldexpf((float)o.xp32, -c.FX) * c.dl_f;
   else if (o.code == AEQC_CODE_ZERO) o.xpf = 0.f;
   else o.xpf = fmaf((float)o.code, c.dl_f, xh);
   return o;
 }
 
-// The lambda-independent moments of one quantization level.
+// The lambda-independent moments of one quantization level, double-float.
 struct Moments {
-  double R[4];   // sum vol phi_k (x - x')
-  double M[10];  // upper triangle of sum vol phi phi^T x'
-  double S[4];   // sum vol |phi_k| x'
+  df R[4];       // sum vol phi_k (x - x')
+  df M[10];      // upper triangle of sum vol phi phi^T x' (m00 m01 m02 m03 m11 ...)
+  float S[4];    // sum vol |phi_k| x'
   unsigned flags;  // CODE_ESCAPE / AE_EXACT
 };
 
 // Quantize the histogram (row xb, decoded row xhb) into shared memory and
 // accumulate its moments.
-__device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb, const float* xhb,
-                        const QConst& c, FastWS& w, Moments& mo, int lane) {
-  long long U0 = 0, U1 = 0, U2 = 0, U3 = 0;
-  long long T00 = 0, T10 = 0, T20 = 0, T30 = 0, T40 = 0, T01 = 0, T11 = 0, T21 = 0, T02 = 0;
+__device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb,
+                        const float* xhb, const QConst& c, FastWS& w, Moments& mo, int lane) {
+  long long U[4] = {0, 0, 0, 0};
+  long long T[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // T00 T10 T20 T30 T40 T01 T11 T21 T02
   float s1 = 0.f;
   int esc = 0, nonzero = 0;
   const float b_f = (float)fg.b, c0_f = (float)fg.c0;
@@ -231,79 +318,91 @@ __device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb, c
     const int ic = it.i - fg.i_c, j2 = it.j * it.j;
     const int ic2 = ic * ic;
     const long long r = o.rho32, X = o.xp32;
-    U0 += r;
-    U1 += r * ic;
-    U2 += r * ic2;
-    U3 += r * j2;
-    T00 += X;
-    T10 += X * ic;
-    T20 += X * ic2;
-    T30 += X * (ic2 * ic);
-    T40 += X * (ic2 * ic2);
-    T01 += X * j2;
-    T11 += X * (ic * j2);
-    T21 += X * (ic2 * j2);
-    T02 += X * (j2 * j2);
+    U[0] += r;
+    U[1] += r * ic;
+    U[2] += r * ic2;
+    U[3] += r * j2;
+    T[0] += X;
+    T[1] += X * ic;
+    T[2] += X * ic2;
+    T[3] += X * (ic2 * ic);
+    T[4] += X * (ic2 * ic2);
+    T[5] += X * j2;
+    T[6] += X * (ic * j2);
+    T[7] += X * (ic2 * j2);
+    T[8] += X * (j2 * j2);
     s1 = fmaf(o.xpf, fabsf(fmaf(b_f, (float)ic, c0_f)), s1);
   }
   __syncwarp();
-  const double u0 = wsum((double)U0), u1 = wsum((double)U1), u2 = wsum((double)U2),
-               u3 = wsum((double)U3);
-  double T[5][3];
-  T[0][0] = wsum((double)T00); T[1][0] = wsum((double)T10); T[2][0] = wsum((double)T20);
-  T[3][0] = wsum((double)T30); T[4][0] = wsum((double)T40);
-  T[0][1] = wsum((double)T01); T[1][1] = wsum((double)T11); T[2][1] = wsum((double)T21);
-  T[0][2] = wsum((double)T02);
-  const double S1 = wsum((double)s1);
-  const double vol = g.vol_uniform, b = fg.b, c0 = fg.c0, d2 = fg.d2;
-  const double sr = vol * ldexp(c.dl, -30), sm = vol * ldexp(c.dl, -c.FX);
-  mo.R[0] = sr * u0;
-  mo.R[1] = sr * (b * u1 + c0 * u0);
-  mo.R[2] = sr * (d2 * u3);
-  mo.R[3] = sr * (b * b * u2 + 2.0 * b * c0 * u1 + c0 * c0 * u0);
-  // m(p, q) = sum x' v^p w^q, v = b ic + c0, w = d2 j^2 (binomial expansion in ic)
+  // per-lane sums stay below 2^60; convert, then add across the warp exactly
+  df u[4], t[9];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) u[q] = df_wsum(df_from_ll(U[q]));
+#pragma unroll
+  for (int q = 0; q < 9; ++q) t[q] = df_wsum(df_from_ll(T[q]));
+  const float S1 = df_wsum(df{s1, 0.f}).hi;
+  const df vol = {fg.vol_h, fg.vol_l};
+  const df sr = df_ldexp(vol, c.k - 30), sm = df_ldexp(vol, c.k - c.FX);
+  const df b = {fg.coef_h[1][1], fg.coef_l[1][1]};   // C(1,1) b = b
+  const df c0 = {fg.coef_h[1][0], fg.coef_l[1][0]};  // C(1,0) c0 = c0
+  const df d2 = {fg.d2q_h[1], fg.d2q_l[1]};
+  // R_k = vol Delta 2^-30 sum phi_k rho32, phi = (1, v, w, v^2), v = b ic + c0
+  mo.R[0] = df_mul(sr, u[0]);
+  mo.R[1] = df_mul(sr, df_add(df_mul(b, u[1]), df_mul(c0, u[0])));
+  mo.R[2] = df_mul(sr, df_mul(d2, u[3]));
+  {
+    const df cc[3] = {{fg.coef_h[2][0], fg.coef_l[2][0]},
+                      {fg.coef_h[2][1], fg.coef_l[2][1]},
+                      {fg.coef_h[2][2], fg.coef_l[2][2]}};
+    df acc = df_mul(cc[0], u[0]);
+    acc = df_add(acc, df_mul(cc[1], u[1]));
+    acc = df_add(acc, df_mul(cc[2], u[2]));
+    mo.R[3] = df_mul(sr, acc);
+  }
+  // m(p, q) = vol Delta 2^-FX d2^q sum_r C(p,r) b^r c0^(p-r) T[r][q]
+  const df* Tq0 = t;      // T[r][0], r = 0..4
+  const df Tq1[3] = {t[5], t[6], t[7]};
   auto mom = [&](int p, int q) {
-    const double binom[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0},
-                                {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
-    double acc = 0.0, bp = 1.0;
+    df acc = {0.f, 0.f};
     for (int r = 0; r <= p; ++r) {
-      double cp = 1.0;
-      for (int e = 0; e < p - r; ++e) cp *= c0;
-      acc += binom[p][r] * bp * cp * T[r][q];
-      bp *= b;
+      const df tr = q == 0 ? Tq0[r] : (q == 1 ? Tq1[r] : t[8]);
+      acc = df_add(acc, df_mul(df{fg.coef_h[p][r], fg.coef_l[p][r]}, tr));
     }
-    double wq = 1.0;
-    for (int e = 0; e < q; ++e) wq *= d2;
-    return sm * wq * acc;
+    return df_mul(sm, df_mul(df{fg.d2q_h[q], fg.d2q_l[q]}, acc));
   };
-  const double m00 = mom(0, 0), m10 = mom(1, 0), m20 = mom(2, 0), m30 = mom(3, 0),
-               m40 = mom(4, 0), m01 = mom(0, 1), m11 = mom(1, 1), m21 = mom(2, 1),
-               m02 = mom(0, 2);
+  const df m00 = mom(0, 0), m10 = mom(1, 0), m20 = mom(2, 0), m30 = mom(3, 0),
+           m40 = mom(4, 0), m01 = mom(0, 1), m11 = mom(1, 1), m21 = mom(2, 1),
+           m02 = mom(0, 2);
   mo.M[0] = m00; mo.M[1] = m10; mo.M[2] = m01; mo.M[3] = m20;
   mo.M[4] = m20; mo.M[5] = m11; mo.M[6] = m30;
   mo.M[7] = m02; mo.M[8] = m21;
   mo.M[9] = m40;
-  mo.S[0] = m00;
-  mo.S[1] = vol * S1;
-  mo.S[2] = m01;
-  mo.S[3] = m20;
+  mo.S[0] = m00.hi;
+  mo.S[1] = fg.vol_h * S1;
+  mo.S[2] = m01.hi;
+  mo.S[3] = m20.hi;
   mo.flags = 0;
   if (__any_sync(FULL, esc)) mo.flags |= AEQC_ST_CODE_ESCAPE;
   if (!__any_sync(FULL, nonzero)) mo.flags |= AEQC_ST_AE_EXACT;
 }
 
 struct PassOut {
-  double H[4];
+  df H[4];
+  float Habs[4];  // sums of |terms| (for the rounding bound of the FP32 sums)
   float tmax;
   int viol, uncertain;
 };
 
-// One FP32 pass at lambda: H(lambda) and the end-to-end check.
-__device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w, const QConst& c,
-                          const double lam[4], float e_lo, float e_hi, PassOut& o, int lane) {
-  const float l0 = (float)lam[0], l1 = (float)lam[1], l2 = (float)lam[2], l3 = (float)lam[3];
+// One pass at lambda: H(lambda) and the end-to-end check.  exact_sums selects
+// TwoSum accumulation of H (used when the FP32 sums' error bound is too wide).
+template <bool EXACT>
+__device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
+                          const QConst& c, const df lam[4], float e_lo, float e_hi, PassOut& o,
+                          int lane) {
+  const float l0 = lam[0].hi, l1 = lam[1].hi, l2 = lam[2].hi, l3 = lam[3].hi;
   const float b_f = (float)fg.b, c0_f = (float)fg.c0, d2_f = (float)fg.d2;
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, tmax = 0.f;
+  df a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  float ab1 = 0.f, tmax = 0.f;
   int viol = 0, unc = 0;
   PointIter it(lane, g.n_par);
   for (; it.p < g.P; it.next()) {
@@ -311,23 +410,35 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w, 
     const float v = fmaf(b_f, (float)(it.i - fg.i_c), c0_f);
     const float wq = d2_f * (float)(it.j * it.j);
     const float t = fmaf(fmaf(l3, v, l1), v, fmaf(l2, wq, l0));
-    const float h = t * t * fmaf(-t, fmaf(-t, fmaf(-t, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f);
+    const float h =
+        t * t * fmaf(-t, fmaf(-t, fmaf(-t, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f);
     const float y = xp * h;
-    a0 += y;
     const float yv = y * v;
-    a1 += yv;
-    a2 = fmaf(y, wq, a2);
-    a3 = fmaf(yv, v, a3);
+    if (EXACT) {
+      a[0] = df_add_f(a[0], y);
+      a[1] = df_add_f(a[1], yv);
+      a[2] = df_add_f(a[2], y * wq);
+      a[3] = df_add_f(a[3], yv * v);
+    } else {
+      a[0].hi += y;
+      a[1].hi += yv;
+      a[2].hi = fmaf(y, wq, a[2].hi);
+      a[3].hi = fmaf(yv, v, a[3].hi);
+    }
+    ab1 += fabsf(yv);
     if (xp > 0.f) tmax = fmaxf(tmax, fabsf(t));
     const float err = fabsf(fmaf(xp, h - t, -c.dl_f * w.rho[it.p]));
     viol |= err > e_hi;
     unc |= err > e_lo;
   }
-  const double vol = g.vol_uniform;
-  o.H[0] = vol * wsum((double)a0);
-  o.H[1] = vol * wsum((double)a1);
-  o.H[2] = vol * wsum((double)a2);
-  o.H[3] = vol * wsum((double)a3);
+  const df vol = {fg.vol_h, fg.vol_l};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.H[k] = df_mul(vol, df_wsum(a[k]));
+  // terms of H_0, H_2, H_3 are >= 0 (h >= 0, x' >= 0): |H_k| is their size
+  o.Habs[0] = fabsf(o.H[0].hi);
+  o.Habs[1] = fg.vol_h * df_wsum(df{ab1, 0.f}).hi;
+  o.Habs[2] = fabsf(o.H[2].hi);
+  o.Habs[3] = fabsf(o.H[3].hi);
   float tm = tmax;
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) tm = fmaxf(tm, __shfl_xor_sync(FULL, tm, s));
@@ -336,82 +447,176 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w, 
   o.uncertain = __any_sync(FULL, unc);
 }
 
-enum { FAST_OK = 0, FAST_DEFER = 1, FAST_CHECK_FAILED = 2, FAST_NOT_CONVERGED = 3 };
-
-struct NewtonState {
-  double lam[4];
-  int iters;
-  int check_viol;  // end-to-end violation at the final lambda (valid when converged)
-  double g[4];
+// FP32 Cholesky of the unit-diagonal scaling of M (the chord Jacobian).
+struct Chol {
+  float L[4][4];
+  float d[4];  // 1 / sqrt(M_kk)
+  bool ok;
 };
 
-// Bound on |t| = |lambda.phi| over the grid (for the check's rounding margin).
-__device__ __forceinline__ double t_bound(const double lam[4], double vmax, double wmax) {
-  return fabs(lam[0]) + fabs(lam[1]) * vmax + fabs(lam[2]) * wmax + fabs(lam[3]) * vmax * vmax;
+__device__ __forceinline__ void chol_factor(const df M[10], Chol& ch) {
+  float a[4][4];
+  const int idx[4][4] = {{0, 1, 2, 3}, {1, 4, 5, 6}, {2, 5, 7, 8}, {3, 6, 8, 9}};
+  ch.ok = true;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float mk = M[idx[k][k]].hi;
+    ch.ok = ch.ok && mk > 0.f;
+    ch.d[k] = mk > 0.f ? rsqrtf(mk) : 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) a[k][l] = M[idx[k][l]].hi * ch.d[k] * ch.d[l];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) ch.L[k][l] = 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int l = 0; l <= k; ++l) {
+      float s = a[k][l];
+#pragma unroll
+      for (int q = 0; q < l; ++q) s = fmaf(-ch.L[k][q], ch.L[l][q], s);
+      if (k == l) {
+        ch.ok = ch.ok && s > 1e-6f;  // cond(M) beyond ~1e6: leave it to FP64
+        ch.L[k][k] = s > 0.f ? sqrtf(s) : 1.f;
+      } else {
+        ch.L[k][l] = s / ch.L[l][l];
+      }
+    }
+  }
 }
+
+// delta = M^-1 r in FP32 through the scaled factorisation
+__device__ __forceinline__ void chol_solve(const Chol& ch, const float r[4], float dlt[4]) {
+  float y[4], z[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float s = r[k] * ch.d[k];
+#pragma unroll
+    for (int q = 0; q < k; ++q) s = fmaf(-ch.L[k][q], y[q], s);
+    y[k] = s / ch.L[k][k];
+  }
+#pragma unroll
+  for (int k = 3; k >= 0; --k) {
+    float s = y[k];
+#pragma unroll
+    for (int q = k + 1; q < 4; ++q) s = fmaf(-ch.L[q][k], z[q], s);
+    z[k] = s / ch.L[k][k];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) dlt[k] = z[k] * ch.d[k];
+}
+
+// (M v)_k in double-float for a float vector v
+__device__ __forceinline__ void df_matvec_f(const df M[10], const float v[4], df out[4]) {
+  const int idx[4][4] = {{0, 1, 2, 3}, {1, 4, 5, 6}, {2, 5, 7, 8}, {3, 6, 8, 9}};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    df acc = df_mul_f(M[idx[k][0]], v[0]);
+#pragma unroll
+    for (int l = 1; l < 4; ++l) acc = df_add(acc, df_mul_f(M[idx[k][l]], v[l]));
+    out[k] = acc;
+  }
+}
+
+// (M lambda)_k in double-float
+__device__ __forceinline__ void df_matvec(const df M[10], const df lam[4], df out[4]) {
+  const int idx[4][4] = {{0, 1, 2, 3}, {1, 4, 5, 6}, {2, 5, 7, 8}, {3, 6, 8, 9}};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    df acc = df_mul(M[idx[k][0]], lam[0]);
+#pragma unroll
+    for (int l = 1; l < 4; ++l) acc = df_add(acc, df_mul(M[idx[k][l]], lam[l]));
+    out[k] = acc;
+  }
+}
+
+struct NewtonState {
+  int check_viol;  // end-to-end violation at the final lambda (valid when converged)
+  float gres[4];   // |g_k| / S_k at the final lambda
+};
 
 // Round 1 of Eq. (6) with the chord Jacobian M from lam (in/out).
 // Returns 1 converged, 0 not converged, -1 defer (precision guards).
 __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
-                           const QConst& c, const Moments& mo, double lam[4], int max_iter,
-                           double step, double tol, double e, double s, double vmax,
-                           double wmax, int* iters, double* r0, double* rlast, NewtonState& ns,
-                           int lane) {
+                           const QConst& c, const Moments& mo, const Chol& ch, df lam[4],
+                           int max_iter, float step, float tol, float e, float s, int* iters,
+                           float* r0, float* rlast, NewtonState& ns, int lane) {
   for (int it = 0;; ++it) {
-    double H[4] = {0.0, 0.0, 0.0, 0.0};
-    const bool zero_lam = lam[0] == 0.0 && lam[1] == 0.0 && lam[2] == 0.0 && lam[3] == 0.0;
+    df H[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    const bool zero_lam =
+        lam[0].hi == 0.f && lam[1].hi == 0.f && lam[2].hi == 0.f && lam[3].hi == 0.f;
     int viol = 0, unc = 0;
-    // pass (also needed at lambda = 0 for the end-to-end check once converged)
     bool did_pass = false;
+    float tmax = 0.f;
     auto do_pass = [&]() {
-      const double tb = t_bound(lam, vmax, wmax);
-      const double margin = 4e-7 * (s * tb + c.dl) + 1e-30;
+      const float tb = fabsf(lam[0].hi) + fabsf(lam[1].hi) * fg.vmax + fabsf(lam[2].hi) * fg.wmax +
+                       fabsf(lam[3].hi) * fg.vmax * fg.vmax;
+      // FP32 rounding of the check (x' e^{-t} - x evaluated as x'(h - t) - Delta rho)
+      const float margin = 4e-7f * (s * tb + c.dl_f) + 1e-30f;
       PassOut po;
-      pass_warp(g, fg, w, c, lam, (float)(e - margin), (float)(e + margin), po, lane);
+      pass_warp<false>(g, fg, w, c, lam, e - margin, e + margin, po, lane);
+      bool redo = false;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)  // 48 FP32 additions per lane: |error| <= 48 u sum|terms|
+        redo = redo || 3e-6f * po.Habs[k] > 1e-13f * mo.S[k];
+      if (redo) pass_warp<true>(g, fg, w, c, lam, e - margin, e + margin, po, lane);
 #pragma unroll
       for (int k = 0; k < 4; ++k) H[k] = po.H[k];
       viol = po.viol;
       unc = po.uncertain;
       did_pass = true;
-      return po.tmax;
+      tmax = po.tmax;
     };
-    float tmax = 0.f;
-    if (!zero_lam) tmax = do_pass();
-    double gk[4];
+    if (!zero_lam) do_pass();
+    df Ml[4];
+    df_matvec(mo.M, lam, Ml);
+    df gk[4];
+    float res = 0.f;
+    bool finite_ok = true;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const double* Mr = mo.M;
-      double ml;
-      switch (k) {
-        case 0: ml = Mr[0] * lam[0] + Mr[1] * lam[1] + Mr[2] * lam[2] + Mr[3] * lam[3]; break;
-        case 1: ml = Mr[1] * lam[0] + Mr[4] * lam[1] + Mr[5] * lam[2] + Mr[6] * lam[3]; break;
-        case 2: ml = Mr[2] * lam[0] + Mr[5] * lam[1] + Mr[7] * lam[2] + Mr[8] * lam[3]; break;
-        default: ml = Mr[3] * lam[0] + Mr[6] * lam[1] + Mr[8] * lam[2] + Mr[9] * lam[3]; break;
-      }
-      gk[k] = -mo.R[k] - ml + H[k];
+      gk[k] = df_add(df_neg(df_add(mo.R[k], Ml[k])), H[k]);
+      const float den = mo.S[k] > 0.f ? mo.S[k] : 1e-30f;
+      const float rk = fabsf(gk[k].hi) / den;
+      finite_ok = finite_ok && isfinite(rk);
+      ns.gres[k] = rk;
+      res = fmaxf(res, rk);
     }
-    const double res = scaled_residual(gk, mo.S);
     if (it == 0) *r0 = res;
     *rlast = res;
     *iters = it;
-    if (!isfinite(res)) return 0;
+    if (!finite_ok) return 0;
     if (tmax > 0.05f) return -1;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      if (fabs(H[k]) > 1e-5 * mo.S[k]) return -1;
+      if (fabsf(H[k].hi) > 1e-5f * mo.S[k]) return -1;
     if (res <= tol) {
       if (!did_pass) do_pass();  // lambda = 0 converged: still check every point
       if (unc && !viol) return -1;
       ns.check_viol = viol;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) ns.g[k] = gk[k];
       return 1;
     }
     if (it == max_iter) return 0;
-    double d[4];
-    if (chol_solve4(mo.M, gk, d) != 0) return 0;
+    // chord step with one refinement: delta = M^-1 g, then M^-1 (g - M delta)
+    float r[4], d1[4], d2[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) lam[k] += step * d[k];
+    for (int k = 0; k < 4; ++k) r[k] = gk[k].hi;
+    chol_solve(ch, r, d1);
+    df Md[4];
+    df_matvec_f(mo.M, d1, Md);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r[k] = df_add(gk[k], df_neg(Md[k])).hi;
+    chol_solve(ch, r, d2);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      lam[k] = df_add_f(lam[k], step * d1[k]);
+      lam[k] = df_add_f(lam[k], step * d2[k]);
+    }
   }
 }
 
@@ -437,18 +642,13 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
   }
   bad = __any_sync(FULL, bad);
   const double s = __longlong_as_double((long long)umax);
-  bool defer = bad || s == 0.0;
-
-  // v_par and v_perp^2 extents for the check margin
-  const double vmax = fabs(fg.b) * (double)((fg.i_c > g.n_par - 1 - fg.i_c) ? fg.i_c
-                                                                            : g.n_par - 1 - fg.i_c) +
-                      fabs(fg.c0);
-  const double wmax = fg.d2 * (double)((g.n_perp - 1) * (g.n_perp - 1));
+  bool defer = bad || umax == 0;
   unsigned st = 0;
-  double lam[4] = {0.0, 0.0, 0.0, 0.0};
+  df lam[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   int total_it = 0;
-  double dfeat[4] = {0.0, 0.0, 0.0, 0.0};
+  float dfeat[4] = {0.f, 0.f, 0.f, 0.f};
   bool done = false;
+  const float s_f = (float)s;
   for (int level = 0; level < 2 && !defer && !done; ++level) {
     QConst c;
     if (!make_qconst(pr.tau, s, level ? pr.alpha * 0.25 : pr.alpha, c)) {
@@ -458,59 +658,59 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
     Moments mo;
     phase_a(g, fg, xb, xhb, c, w, mo, lane);
     st = mo.flags | (level ? AEQC_ST_ALPHA_RETRY : 0u) | (st & AEQC_ST_WARM_REJECTED);
+    Chol ch;
+    chol_factor(mo.M, ch);
+    if (!ch.ok) {
+      defer = true;
+      break;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) lam[k] = df{0.f, 0.f};
     int warm = 0;
     if (level == 0) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const double den = mo.S[k] > 0.0 ? mo.S[k] : 1e-300;
-        dfeat[k] = mo.R[k] / den;
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) lam[k] = 0.0;
+      for (int k = 0; k < 4; ++k)
+        dfeat[k] = mo.S[k] > 0.f ? mo.R[k].hi / mo.S[k] : 0.f;
       if (a.use_mlp) {
         const int L = a.latent.L;
+        double l0[4];
         mlp_eval_warp(
-            a.mlp,
-            [&](int k) { return k < L ? load_latent(a.latent, b, k) : (float)dfeat[k - L]; },
-            lam, lane);
+            a.mlp, [&](int k) { return k < L ? load_latent(a.latent, b, k) : dfeat[k - L]; },
+            l0, lane);
         warm = 1;
-        bool ok = true;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) ok = ok && isfinite(lam[k]);
-        if (!ok) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) lam[k] = 0.0;
-          warm = 0;
-          st |= AEQC_ST_WARM_REJECTED;
+        for (int k = 0; k < 4; ++k) {
+          const float v = (float)l0[k];
+          warm = warm && isfinite(v);
+          lam[k] = df{isfinite(v) ? v : 0.f, 0.f};
         }
+        if (!warm) st |= AEQC_ST_WARM_REJECTED;
       }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) lam[k] = 0.0;
     }
-    const double e = pr.tau * s;
+    const float e = (float)(pr.tau * s);
     NewtonState ns;
     ns.check_viol = 0;
     int conv, it1 = 0, itw = 0;
-    double r0 = 0.0, rw = 0.0, rdummy, rdummy2;
+    float r0 = 0.f, rw = 0.f, rd0, rd1;
+    const float tol = (float)pr.tol, step = (float)pr.step_s;
     if (warm) {
-      conv = round1_fast(g, fg, w, c, mo, lam, pr.warm_iters, pr.step_s, pr.tol, e, s, vmax,
-                         wmax, &itw, &r0, &rw, ns, lane);
+      conv = round1_fast(g, fg, w, c, mo, ch, lam, pr.warm_iters, step, tol, e, s_f, &itw, &r0,
+                         &rw, ns, lane);
       if (conv == 0) {
-        if (!isfinite(rw) || !isfinite(r0) || rw > pr.warm_reject || rw > r0) {
+        if (!isfinite(rw) || !isfinite(r0) || rw > (float)pr.warm_reject || rw > r0) {
           st |= AEQC_ST_WARM_REJECTED;
 #pragma unroll
-          for (int k = 0; k < 4; ++k) lam[k] = 0.0;
-          conv = round1_fast(g, fg, w, c, mo, lam, pr.max_iter, pr.step_s, pr.tol, e, s, vmax,
-                             wmax, &it1, &rdummy, &rdummy2, ns, lane);
+          for (int k = 0; k < 4; ++k) lam[k] = df{0.f, 0.f};
+          conv = round1_fast(g, fg, w, c, mo, ch, lam, pr.max_iter, step, tol, e, s_f, &it1,
+                             &rd0, &rd1, ns, lane);
         } else {
-          conv = round1_fast(g, fg, w, c, mo, lam, pr.max_iter - pr.warm_iters, pr.step_s,
-                             pr.tol, e, s, vmax, wmax, &it1, &rdummy, &rdummy2, ns, lane);
+          conv = round1_fast(g, fg, w, c, mo, ch, lam, pr.max_iter - pr.warm_iters, step, tol,
+                             e, s_f, &it1, &rd0, &rd1, ns, lane);
         }
       }
     } else {
-      conv = round1_fast(g, fg, w, c, mo, lam, pr.max_iter, pr.step_s, pr.tol, e, s, vmax,
-                         wmax, &it1, &r0, &rdummy2, ns, lane);
+      conv = round1_fast(g, fg, w, c, mo, ch, lam, pr.max_iter, step, tol, e, s_f, &it1, &r0,
+                         &rd1, ns, lane);
     }
     total_it += itw + it1;
     if (conv != 1) {  // round 2 and verbatim storage belong to the FP64 kernel
@@ -520,15 +720,9 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
     st |= AEQC_ST_CONVERGED;
     bool qoi_ok = true;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const double den = mo.S[k] > 0.0 ? mo.S[k] : 1e-300;
-      qoi_ok = qoi_ok && fabs(ns.g[k]) / den <= pr.qoi_check;
-    }
-    if (!ns.check_viol && qoi_ok) {
-      done = true;
-    } else if (level == 1) {
-      defer = true;  // verbatim after the retry: the FP64 kernel stores it
-    }
+    for (int k = 0; k < 4; ++k) qoi_ok = qoi_ok && ns.gres[k] <= (float)pr.qoi_check;
+    if (!ns.check_viol && qoi_ok) done = true;
+    else if (level == 1) defer = true;  // verbatim after the retry: the FP64 kernel stores it
   }
   if (defer || !done) {
     if (lane == 0) {
@@ -538,16 +732,27 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
     __syncwarp();
     return;
   }
+  // the multipliers as float64: lane k converts lambda_k (one warp instruction
+  // sequence serves all four)
+  double lamd = 0.0;
+  {
+    const int k = lane & 3;
+    const df lk = k == 0 ? lam[0] : (k == 1 ? lam[1] : (k == 2 ? lam[2] : lam[3]));
+    lamd = (double)lk.hi + (double)lk.lo;
+  }
   // outputs
   int16_t* cb = a.codes + b * (long long)P;
   for (int p = lane; p < P; p += 32) cb[p] = w.codes[p];
   if (a.f_out) {
     // f = x' exp(-lambda.phi) with the rounding of the decompression kernel
-    for (int i = lane; i < g.n_par; i += 32) w.ta[i] = corr_a(lam, g.vpar[i]);
-    for (int j = lane; j < g.n_perp; j += 32) w.tb[j] = corr_b(lam, g.vperp2[j]);
+    double ld[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ld[k] = __shfl_sync(FULL, lamd, k);
+    for (int i = lane; i < g.n_par; i += 32) w.ta[i] = corr_a(ld, g.vpar[i]);
+    for (int j = lane; j < g.n_perp; j += 32) w.tb[j] = corr_b(ld, g.vperp2[j]);
     __syncwarp();
-    const double dl = bin_width(pr.tau, s, (st & AEQC_ST_ALPHA_RETRY) ? pr.alpha * 0.25
-                                                                     : pr.alpha);
+    const double dl =
+        bin_width(pr.tau, s, (st & AEQC_ST_ALPHA_RETRY) ? pr.alpha * 0.25 : pr.alpha);
     double* fb = a.f_out + b * (long long)P;
     PointIter pi(lane, g.n_par);
     for (; pi.p < P; pi.next()) {
@@ -565,14 +770,13 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
   if (a.features) {
     float* fr = a.features + b * (long long)(a.latent.L + 4);
     for (int l = lane; l < a.latent.L; l += 32) fr[l] = load_latent(a.latent, b, l);
-    if (lane < 4) fr[a.latent.L + lane] = (float)dfeat[lane];
+    if (lane < 4) fr[a.latent.L + lane] = dfeat[lane];
   }
+  if (lane < 4) a.lambda[b * 4 + lane] = lamd;
   if (lane == 0) {
     a.scale[b] = s;
     a.iters[b] = (uint8_t)(total_it > 255 ? 255 : total_it);
     a.status[b] = (uint16_t)st;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) a.lambda[b * 4 + k] = lam[k];
   }
   __syncwarp();
 }
@@ -586,21 +790,26 @@ __global__ void __launch_bounds__(FW * 32) fused_fast_kernel(const FusedArgs a) 
     fast_histogram(a, w, b, lane);
 }
 
+void split_df(double v, float* h, float* l) {
+  *h = (float)v;
+  *l = (float)(v - (double)*h);
+}
+
 }  // namespace
 
 int make_fast_grid(const GridK& g, FastGridK* out) {
   FastGridK f;
-  f.ok = 0;
-  f.i_c = 0;
-  f.b = f.c0 = f.d2 = 0.0;
+  memset(&f, 0, sizeof(f));
   *out = f;
   if (g.has_vol || g.n_par < 2 || g.n_perp < 2) return AEQC_OK;
+  // integer weights must stay below 2^24 (|i - i_c|^4, j^4) and the x' sums
+  // of one lane below 2^62
+  if (g.n_par > 64 || g.n_perp > 64) return AEQC_OK;
   const double b = (g.vpar[g.n_par - 1] - g.vpar[0]) / (double)(g.n_par - 1);
   if (!(b > 0.0)) return AEQC_OK;
   double vmax = 0.0;
   for (int i = 0; i < g.n_par; ++i) vmax = fmax(vmax, fabs(g.vpar[i]));
-  // index nearest to v_par = 0
-  int ic = (int)llround(-g.vpar[0] / b);
+  int ic = (int)llround(-g.vpar[0] / b);  // index nearest to v_par = 0
   if (ic < 0) ic = 0;
   if (ic > g.n_par - 1) ic = g.n_par - 1;
   const double c0 = g.vpar[ic];
@@ -617,6 +826,19 @@ int make_fast_grid(const GridK& g, FastGridK* out) {
   f.b = b;
   f.c0 = c0;
   f.d2 = d2;
+  split_df(g.vol_uniform, &f.vol_h, &f.vol_l);
+  split_df(1.0, &f.d2q_h[0], &f.d2q_l[0]);
+  split_df(d2, &f.d2q_h[1], &f.d2q_l[1]);
+  split_df(d2 * d2, &f.d2q_h[2], &f.d2q_l[2]);
+  const double binom[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0},
+                              {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+  for (int p = 0; p < 5; ++p)
+    for (int r = 0; r < 5; ++r) {
+      const double cf = r <= p ? binom[p][r] * pow(b, r) * pow(c0, p - r) : 0.0;
+      split_df(cf, &f.coef_h[p][r], &f.coef_l[p][r]);
+    }
+  f.vmax = (float)vmax;
+  f.wmax = (float)g.vperp2[g.n_perp - 1];
   *out = f;
   return AEQC_OK;
 }

@@ -137,12 +137,16 @@ def lam_metric_close(a, b, xp, og, slack=3e-12):
     vp = np.tile(og.vpar, len(og.vperp))
     vq = np.repeat(og.vperp, len(og.vpar)) ** 2
     phi = np.stack([np.ones_like(vp), vp, vq, vp * vp])
+    worst, wrow = 0.0, -1
     for r in range(len(a)):
         M = og.vol_uniform * (phi * xp[r]) @ phi.T
         S = og.vol_uniform * (np.abs(phi) * xp[r]).sum(1)
-        if np.any(np.abs(M @ (a[r] - b[r])) > slack * S):
-            return False
-    return True
+        e = np.max(np.abs(M @ (a[r] - b[r])) / S)
+        if e > worst:
+            worst, wrow = e, r
+    if worst > slack:
+        print("lambda metric: worst %.3e at row %d: %s vs %s" % (worst, wrow, a[wrow], b[wrow]))
+    return worst <= slack
 
 
 def xprime_at_level(x, xh, tau, status):

@@ -187,20 +187,22 @@ struct QConst {
   long long half, mask;
 };
 
-__device__ __forceinline__ bool make_qconst(double tau, double s, double alpha, QConst& c) {
+__device__ __forceinline__ bool make_qconst(double tau, double s, double alpha, int xbits,
+                                            QConst& c) {
   c.dl = bin_width(tau, s, alpha);
   if (!(c.dl > 0.0) || !isfinite(c.dl)) return false;
   c.k = exponent_of(c.dl) - 1;
   const int IBx = exponent_of(s) - c.k;  // s / Delta < 2^IBx
   const int IB = (IBx > 15 ? IBx : 15) + 2;
   c.F = 62 - IB;
-  c.FX = 30 - IBx;
+  c.FX = xbits - IBx;
   c.thr = c.k + IB - 1;
   c.half = 1ll << (c.F - 1);
   c.mask = (1ll << c.F) - 1;
   // float copies: Delta and the scale factors of the moment sums must be
   // normal floats (moments are scaled by vol Delta 2^-30 and vol Delta 2^-FX)
-  const bool ok = c.F >= 31 && c.FX >= 1 && IBx >= 1 && c.k - 40 >= -100 && c.k + 20 <= 100;
+  const bool ok = c.F >= 31 && c.FX >= 1 && c.F - c.FX >= 1 && IBx >= 1 &&
+                  c.k - 64 >= -100 && c.k + 20 <= 100;
   c.dl_f = ok ? exp2i(c.k) : 0.f;
   return ok;
 }
@@ -208,7 +210,7 @@ __device__ __forceinline__ bool make_qconst(double tau, double s, double alpha, 
 struct PointQ {
   int code;
   int rho32;  // round((x - x') / Delta * 2^30)
-  int xp32;   // round(x' / Delta * 2^FX)
+  long long xpw;  // round(x' / Delta * 2^FX)
   float xpf;  // x' (float)
 };
 
@@ -274,15 +276,15 @@ __device__ __forceinline__ PointQ quant_point_int(double x, float xh, const QCon
     o.code = quant_point_fp64(x, (double)xh, c.dl, &xpd);
     const double rd = __ddiv_rn(__dsub_rn(x, xpd), c.dl);
     o.rho32 = __double2int_rn(ldexp(rd, 30));
-    o.xp32 = __double2int_rn(ldexp(__ddiv_rn(xpd, c.dl), c.FX));
+    o.xpw = __double2ll_rn(ldexp(__ddiv_rn(xpd, c.dl), c.FX));
     o.xpf = (float)xpd;
     return o;
   }
   // round to nearest: a floor would bias every cell the same way, and the
   // high-order weights (v^4 up to 256) would turn that into a systematic error
   o.rho32 = (int)((rho_fix + (1ll << (c.F - 31))) >> (c.F - 30));
-  o.xp32 = (int)((xp_fix + (1ll << (c.F - c.FX - 1))) >> (c.F - c.FX));
-  if (o.code == AEQC_CODE_ESCAPE) o.xpf = ldexpf((float)o.xp32, -c.FX) * c.dl_f;
+  o.xpw = (xp_fix + (1ll << (c.F - c.FX - 1))) >> (c.F - c.FX);
+  if (o.code == AEQC_CODE_ESCAPE) o.xpf = ldexpf((float)o.xpw, -c.FX) * c.dl_f;
   else if (o.code == AEQC_CODE_ZERO) o.xpf = 0.f;
   else o.xpf = fmaf((float)o.code, c.dl_f, xh);
   return o;
@@ -317,7 +319,7 @@ __device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb,
     nonzero |= o.code != 0;
     const int ic = it.i - fg.i_c, j2 = it.j * it.j;
     const int ic2 = ic * ic;
-    const long long r = o.rho32, X = o.xp32;
+    const long long r = o.rho32, X = o.xpw;
     U[0] += r;
     U[1] += r * ic;
     U[2] += r * ic2;
@@ -388,57 +390,102 @@ __device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb,
 
 struct PassOut {
   df H[4];
-  float Habs[4];  // sums of |terms| (for the rounding bound of the FP32 sums)
+  float Habs[4];  // bounds on the sums of |terms| (for the FP32 rounding bound)
   float tmax;
   int viol, uncertain;
 };
 
-// One pass at lambda: H(lambda) and the end-to-end check.  exact_sums selects
+// t = lambda.phi in exact integer weights: t = a0 + a1 ic + a3 ic^2 + a2 j^2
+// (ic = i - i_c), the coefficients as float pairs so that no weight carries a
+// systematic rounding error.
+struct TCoef {
+  float h[4], l[4];  // a0, a1, a2 (j^2), a3 (ic^2)
+};
+
+__device__ __forceinline__ TCoef make_tcoef(const FastGridK& fg, const df lam[4]) {
+  const df c0 = {fg.coef_h[1][0], fg.coef_l[1][0]}, b = {fg.coef_h[1][1], fg.coef_l[1][1]};
+  const df c00 = {fg.coef_h[2][0], fg.coef_l[2][0]}, c21 = {fg.coef_h[2][1], fg.coef_l[2][1]};
+  const df bb = {fg.coef_h[2][2], fg.coef_l[2][2]}, d2 = {fg.d2q_h[1], fg.d2q_l[1]};
+  const df a0 = df_add(lam[0], df_add(df_mul(lam[1], c0), df_mul(lam[3], c00)));
+  const df a1 = df_add(df_mul(lam[1], b), df_mul(lam[3], c21));
+  const df a2 = df_mul(lam[2], d2);
+  const df a3 = df_mul(lam[3], bb);
+  TCoef t;
+  t.h[0] = a0.hi; t.l[0] = a0.lo;
+  t.h[1] = a1.hi; t.l[1] = a1.lo;
+  t.h[2] = a2.hi; t.l[2] = a2.lo;
+  t.h[3] = a3.hi; t.l[3] = a3.lo;
+  return t;
+}
+
+// One pass at lambda: H(lambda) and the end-to-end check.  EXACT selects
 // TwoSum accumulation of H (used when the FP32 sums' error bound is too wide).
 template <bool EXACT>
 __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
-                          const QConst& c, const df lam[4], float e_lo, float e_hi, PassOut& o,
+                          const QConst& c, const TCoef& tc, float e_lo, float e_hi, PassOut& o,
                           int lane) {
-  const float l0 = lam[0].hi, l1 = lam[1].hi, l2 = lam[2].hi, l3 = lam[3].hi;
-  const float b_f = (float)fg.b, c0_f = (float)fg.c0, d2_f = (float)fg.d2;
-  df a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  df a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};  // sums of y, y ic, y ic^2, y j^2
   float ab1 = 0.f, tmax = 0.f;
   int viol = 0, unc = 0;
-  PointIter it(lane, g.n_par);
-  for (; it.p < g.P; it.next()) {
-    const float xp = w.xp[it.p];
-    const float v = fmaf(b_f, (float)(it.i - fg.i_c), c0_f);
-    const float wq = d2_f * (float)(it.j * it.j);
-    const float t = fmaf(fmaf(l3, v, l1), v, fmaf(l2, wq, l0));
+  // walk p = lane, lane + 32, ... keeping ic and j^2 as exact floats
+  int i = lane % g.n_par, j = lane / g.n_par;
+  float icf = (float)(i - fg.i_c), jf = (float)j, j2f = jf * jf;
+  const float npf = (float)g.n_par;
+  for (int p = lane; p < g.P;) {
+    const float xp = w.xp[p];
+    const float ic2f = icf * icf;
+    const float th = fmaf(tc.h[3], ic2f, fmaf(tc.h[1], icf, fmaf(tc.h[2], j2f, tc.h[0])));
+    const float tl = fmaf(tc.l[3], ic2f, fmaf(tc.l[1], icf, fmaf(tc.l[2], j2f, tc.l[0])));
+    const float t = th + tl;
     const float h =
         t * t * fmaf(-t, fmaf(-t, fmaf(-t, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f);
     const float y = xp * h;
-    const float yv = y * v;
+    const float yi = y * icf;
     if (EXACT) {
       a[0] = df_add_f(a[0], y);
-      a[1] = df_add_f(a[1], yv);
-      a[2] = df_add_f(a[2], y * wq);
-      a[3] = df_add_f(a[3], yv * v);
+      a[1] = df_add_f(a[1], yi);
+      a[2] = df_add_f(a[2], yi * icf);
+      a[3] = df_add_f(a[3], y * j2f);
     } else {
       a[0].hi += y;
-      a[1].hi += yv;
-      a[2].hi = fmaf(y, wq, a[2].hi);
-      a[3].hi = fmaf(yv, v, a[3].hi);
+      a[1].hi += yi;
+      a[2].hi = fmaf(yi, icf, a[2].hi);
+      a[3].hi = fmaf(y, j2f, a[3].hi);
     }
-    ab1 += fabsf(yv);
+    ab1 += fabsf(yi);
     if (xp > 0.f) tmax = fmaxf(tmax, fabsf(t));
-    const float err = fabsf(fmaf(xp, h - t, -c.dl_f * w.rho[it.p]));
+    const float err = fabsf(fmaf(xp, h - t, -c.dl_f * w.rho[p]));
     viol |= err > e_hi;
     unc |= err > e_lo;
+    p += 32;
+    i += 32;
+    icf += 32.f;
+    while (i >= g.n_par) {
+      i -= g.n_par;
+      icf -= npf;
+      j2f = fmaf(2.f, jf, j2f + 1.f);  // (j + 1)^2
+      jf += 1.f;
+    }
   }
-  const df vol = {fg.vol_h, fg.vol_l};
+  df A[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) o.H[k] = df_mul(vol, df_wsum(a[k]));
-  // terms of H_0, H_2, H_3 are >= 0 (h >= 0, x' >= 0): |H_k| is their size
-  o.Habs[0] = fabsf(o.H[0].hi);
-  o.Habs[1] = fg.vol_h * df_wsum(df{ab1, 0.f}).hi;
-  o.Habs[2] = fabsf(o.H[2].hi);
-  o.Habs[3] = fabsf(o.H[3].hi);
+  for (int k = 0; k < 4; ++k) A[k] = df_wsum(a[k]);
+  const float B1 = df_wsum(df{ab1, 0.f}).hi;
+  const df vol = {fg.vol_h, fg.vol_l};
+  const df c0 = {fg.coef_h[1][0], fg.coef_l[1][0]}, b = {fg.coef_h[1][1], fg.coef_l[1][1]};
+  const df c00 = {fg.coef_h[2][0], fg.coef_l[2][0]}, c21 = {fg.coef_h[2][1], fg.coef_l[2][1]};
+  const df bb = {fg.coef_h[2][2], fg.coef_l[2][2]}, d2 = {fg.d2q_h[1], fg.d2q_l[1]};
+  // H_k = vol sum phi_k y with phi = (1, v, w, v^2), v = b ic + c0, w = d2 j^2
+  o.H[0] = df_mul(vol, A[0]);
+  o.H[1] = df_mul(vol, df_add(df_mul(b, A[1]), df_mul(c0, A[0])));
+  o.H[2] = df_mul(vol, df_mul(d2, A[3]));
+  o.H[3] = df_mul(vol, df_add(df_add(df_mul(bb, A[2]), df_mul(c21, A[1])), df_mul(c00, A[0])));
+  // y >= 0 (h >= 0, x' >= 0), so A0, A2, A3 are sums of non-negative terms
+  const float vh = fg.vol_h;
+  o.Habs[0] = vh * fabsf(A[0].hi);
+  o.Habs[1] = vh * (fabsf(b.hi) * B1 + fabsf(c0.hi) * fabsf(A[0].hi));
+  o.Habs[2] = vh * d2.hi * fabsf(A[3].hi);
+  o.Habs[3] = vh * (bb.hi * fabsf(A[2].hi) + fabsf(c21.hi) * B1 + c00.hi * fabsf(A[0].hi));
   float tm = tmax;
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) tm = fmaxf(tm, __shfl_xor_sync(FULL, tm, s));
@@ -559,12 +606,13 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
       // FP32 rounding of the check (x' e^{-t} - x evaluated as x'(h - t) - Delta rho)
       const float margin = 4e-7f * (s * tb + c.dl_f) + 1e-30f;
       PassOut po;
-      pass_warp<false>(g, fg, w, c, lam, e - margin, e + margin, po, lane);
+      const TCoef tc = make_tcoef(fg, lam);
+      pass_warp<false>(g, fg, w, c, tc, e - margin, e + margin, po, lane);
       bool redo = false;
 #pragma unroll
       for (int k = 0; k < 4; ++k)  // 48 FP32 additions per lane: |error| <= 48 u sum|terms|
         redo = redo || 3e-6f * po.Habs[k] > 1e-13f * mo.S[k];
-      if (redo) pass_warp<true>(g, fg, w, c, lam, e - margin, e + margin, po, lane);
+      if (redo) pass_warp<true>(g, fg, w, c, tc, e - margin, e + margin, po, lane);
 #pragma unroll
       for (int k = 0; k < 4; ++k) H[k] = po.H[k];
       viol = po.viol;
@@ -651,7 +699,7 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
   const float s_f = (float)s;
   for (int level = 0; level < 2 && !defer && !done; ++level) {
     QConst c;
-    if (!make_qconst(pr.tau, s, level ? pr.alpha * 0.25 : pr.alpha, c)) {
+    if (!make_qconst(pr.tau, s, level ? pr.alpha * 0.25 : pr.alpha, fg.xbits, c)) {
       defer = true;
       break;
     }
@@ -839,6 +887,21 @@ int make_fast_grid(const GridK& g, FastGridK* out) {
     }
   f.vmax = (float)vmax;
   f.wmax = (float)g.vperp2[g.n_perp - 1];
+  // x' bits: the largest integer weight (|i - i_c|^4, j^4, |i - i_c|^2 j^2)
+  // times the points of one lane must stay below 2^62
+  {
+    const long long icm = ic > g.n_par - 1 - ic ? ic : g.n_par - 1 - ic;
+    const long long jm = g.n_perp - 1;
+    long long wmaxi = icm * icm * icm * icm;
+    if (jm * jm * jm * jm > wmaxi) wmaxi = jm * jm * jm * jm;
+    if (icm * icm * jm * jm > wmaxi) wmaxi = icm * icm * jm * jm;
+    int bw = 0;
+    while ((1ll << bw) <= wmaxi) ++bw;
+    const int per_lane = (g.n_par * g.n_perp + 31) / 32;
+    int bn = 0;
+    while ((1 << bn) < per_lane) ++bn;
+    f.xbits = 62 - bw - bn;
+  }
   *out = f;
   return AEQC_OK;
 }

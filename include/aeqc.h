@@ -291,6 +291,33 @@ int quantize_correct(const aeqc_grid* grid, const double* x, const float* xhat, 
                      double* f_out, void* workspace, size_t workspace_bytes, void* stream);
 size_t quantize_correct_workspace_size(int64_t n);
 
+/* quantize_correct without a caller workspace, for callers that cannot
+ * allocate device memory at the point of the call (an allocator-free serving
+ * loop, code that runs while another component owns the device memory
+ * pool).  The paper has no counterpart: this is a deployment variant of
+ * the call above, with the same arguments (minus the workspace), the same
+ * kernels and the same results.
+ *
+ * Its scratch (the list of histograms the fast kernel hands to the FP64
+ * kernel, and that list's count) lives in one file-scope device array of
+ * the library, sized for AEQC_QC_NOALLOC_MAX_N histograms (about 1 MiB);
+ * n above that limit returns AEQC_EINVAL (split the batch).  Nothing is
+ * allocated: no cudaMalloc/cudaFree and no allocating library routine.
+ * The count is reset on the caller's stream at the start of each call; the
+ * list needs no clearing.
+ *
+ * The first call on each device (with that device current) looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Every call in the process shares the one
+ * array: calls that may overlap on the device (different streams without
+ * ordering between them, or concurrent host threads) race on it and give
+ * wrong results; serialise them (one stream, or an event between calls). */
+#define AEQC_QC_NOALLOC_MAX_N 262144
+int quantize_correct_noalloc(const aeqc_grid* grid, const double* x, const float* xhat,
+                             int64_t ld, int64_t n, const aeqc_params* params,
+                             aeqc_mlp* mlp, int32_t latent_dtype, int32_t latent_dim,
+                             aeqc_compressed* out, double* f_out, void* stream);
+
 /* Compression of n histograms (Stages 3-5): encode, decode, targets Q(x),
  * quantize against the decoded xhat, Newton correction (warm-started by
  * `mlp` when non-NULL), end-to-end check (|f - x| <= e at every point and

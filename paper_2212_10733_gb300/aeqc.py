@@ -121,6 +121,9 @@ SYMBOLS = {
                                    C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "quantize_correct_workspace_size": (C.c_size_t, [C.c_int64]),
+    "quantize_correct_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                           C.c_int64, C.c_void_p, C.c_void_p, C.c_int32,
+                                           C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "decompress_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                                    C.c_void_p]),
@@ -498,6 +501,37 @@ def quantize_correct(grid: Grid, x, xhat, params: aeqc_params, mlp: Optional[MLP
                                    C.byref(params), mlp.h if mlp is not None else None, ldt,
                                    L, C.byref(out.c), _ptr(f), _ptr(ws), ws.numel(),
                                    _stream(stream)))
+    out.f = f
+    return out
+
+
+QC_NOALLOC_MAX_N = 262144  # AEQC_QC_NOALLOC_MAX_N
+
+
+def quantize_correct_noalloc(grid: Grid, x, xhat, params: aeqc_params,
+                             mlp: Optional[MLP] = None, latent=None,
+                             out: Optional[Compressed] = None,
+                             outlier_capacity: Optional[int] = None, features: bool = False,
+                             want_f: bool = False, stream=None):
+    """quantize_correct with the library's static scratch instead of a
+    workspace (n <= QC_NOALLOC_MAX_N; calls must not overlap on the device).
+    The output buffers are still the caller's: pass `out` (and no want_f) to
+    make the call itself allocate nothing."""
+    import torch
+    n, P = x.shape
+    L = latent.shape[1] if latent is not None else 0
+    if out is None:
+        cap = outlier_capacity if outlier_capacity is not None else max(1024, n * 4)
+        out = Compressed(n, P, max(L, 1), torch.float32, x.device, cap, features and L > 0)
+        if latent is not None:
+            out.latent = latent
+            out.c.latent = _ptr(latent)
+    ldt = DTYPE_BF16 if (latent is not None and latent.dtype == torch.bfloat16) else DTYPE_F32
+    f = torch.empty((n, P), dtype=torch.float64, device=x.device) if want_f else None
+    _check(load().quantize_correct_noalloc(C.byref(grid.c), _ptr(x), _ptr(xhat),
+                                           xhat.stride(0), n, C.byref(params),
+                                           mlp.h if mlp is not None else None, ldt, L,
+                                           C.byref(out.c), _ptr(f), _stream(stream)))
     out.f = f
     return out
 

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <mutex>
 
 #include "model.cuh"
 #include "workspace.cuh"
@@ -416,4 +417,56 @@ extern "C" int decompress_batch(aeqc_model* m, const aeqc_grid* grid,
   OutliersK ok = make_outliers(&in->outliers);
   return launch_apply(gk, xhat, AEQC_XHAT_LD, in->codes, in->outliers.count ? &ok : nullptr,
                       in->scale, in->lambda, in->status, n, 0, pk, f, s);
+}
+
+// ---- quantize_correct without a caller workspace -----------------------------
+// The scratch of quantize_correct (deferred-histogram list + its count, laid
+// out exactly as qc_ws(AEQC_QC_NOALLOC_MAX_N) carves it) in one file-scope
+// device array; every call shares it.
+
+namespace aeqc {
+
+constexpr size_t kNoAllocScratchBytes =
+    (sizeof(int) * (size_t)AEQC_QC_NOALLOC_MAX_N + kWsAlign - 1) / kWsAlign * kWsAlign +
+    kWsAlign;
+
+static __device__ __align__(256) char g_qc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_qc_scratch_mu;
+static char* g_qc_scratch_ptr[kNoAllocMaxDevices] = {};
+
+// Address of the array on the current device, looked up once per device.
+static int qc_scratch_current_device(char** out) {
+  int dev = 0;
+  AEQC_CUDA_TRY(cudaGetDevice(&dev));
+  AEQC_CHECK_ARG(dev >= 0 && dev < kNoAllocMaxDevices,
+                 "quantize_correct_noalloc: device ordinal %d >= %d", dev, kNoAllocMaxDevices);
+  std::lock_guard<std::mutex> lock(g_qc_scratch_mu);
+  if (!g_qc_scratch_ptr[dev]) {
+    void* p = nullptr;
+    AEQC_CUDA_TRY(cudaGetSymbolAddress(&p, g_qc_scratch));
+    g_qc_scratch_ptr[dev] = static_cast<char*>(p);
+  }
+  *out = g_qc_scratch_ptr[dev];
+  return AEQC_OK;
+}
+
+}  // namespace aeqc
+
+extern "C" int quantize_correct_noalloc(const aeqc_grid* grid, const double* x,
+                                        const float* xhat, int64_t ld, int64_t n,
+                                        const aeqc_params* params, aeqc_mlp* mlp,
+                                        int32_t latent_dtype, int32_t latent_dim,
+                                        aeqc_compressed* out, double* f_out, void* stream) {
+  clear_error();
+  AEQC_CHECK_ARG(n <= AEQC_QC_NOALLOC_MAX_N,
+                 "quantize_correct_noalloc: n=%lld exceeds the static scratch limit of %d "
+                 "histograms; split the batch or use quantize_correct",
+                 (long long)n, AEQC_QC_NOALLOC_MAX_N);
+  char* scratch = nullptr;
+  int rc = qc_scratch_current_device(&scratch);
+  if (rc) return rc;
+  return quantize_correct(grid, x, xhat, ld, n, params, mlp, latent_dtype, latent_dim, out,
+                          f_out, scratch, kNoAllocScratchBytes, stream);
 }

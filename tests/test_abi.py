@@ -73,3 +73,16 @@ def test_argument_errors_are_caught_on_the_host(lib):
     h = C.c_void_p()
     assert lib.aeqc_model_create(C.byref(d), C.byref(h)) == aeqc.EINVAL
     assert b"H=100" in lib.aeqc_last_error()
+
+
+def test_noalloc_rejects_batches_above_its_static_limit(lib):
+    from paper_2212_10733_gb300 import aeqc, synth
+    vpar, vperp, vol = synth.grid_arrays()
+    g = aeqc.Grid(vpar, vperp, vol)
+    p = aeqc.params_default(kernel=aeqc.KERNEL_FAST)
+    n = aeqc.QC_NOALLOC_MAX_N + 1
+    rc = lib.quantize_correct_noalloc(C.byref(g.c), None, None, 1536, n, C.byref(p), None, 0,
+                                      0, None, None, None)
+    assert rc == aeqc.EINVAL and b"static scratch limit" in lib.aeqc_last_error()
+    header = open(HEADER).read()
+    assert re.search(r"#define AEQC_QC_NOALLOC_MAX_N %d\b" % aeqc.QC_NOALLOC_MAX_N, header)

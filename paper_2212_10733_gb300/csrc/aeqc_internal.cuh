@@ -111,8 +111,6 @@ struct FastGridK {
   float d2q_h[3], d2q_l[3];
   float coef_h[5][5], coef_l[5][5];
   float vmax, wmax;  // max |v_par| and max v_perp^2 on the grid
-  int xbits;         // bits of x' (units of Delta) in the moment sums: the
-                     // largest weight times the points of one lane stays below 2^62
 };
 int make_fast_grid(const GridK& g, FastGridK* out);
 

@@ -44,11 +44,20 @@ using namespace dev;
 constexpr int FW = 4;  // warps per CTA
 
 struct FastWS {
-  float xp[AEQC_MAX_P];   // x' (float) for the Newton passes
-  float rho[AEQC_MAX_P];  // (x - x') / Delta (float) for the end-to-end check
-  int16_t codes[AEQC_MAX_P];
-  double ta[AEQC_MAX_NPAR], tb[AEQC_MAX_NPERP];  // exponential tables for f_out
+  float xp[AEQC_MAX_P];  // x' (float) for the Newton passes
+  union {
+    int16_t rho[AEQC_MAX_P];  // round((x - x') / Delta 2^15) for the end-to-end check
+    struct {
+      double ta[AEQC_MAX_NPAR], tb[AEQC_MAX_NPERP];  // exponential tables for f_out
+    } t;
+  };
 };
+
+// float(v) for |v| < 2^22 without a conversion instruction (those issue to the
+// slow FP64 pipe on this GPU): 1.5 2^23 + v is exact and read off its bits
+__device__ __forceinline__ float small_int_to_float(int v) {
+  return __int_as_float(0x4B400000 + v) - 12582912.f;
+}
 
 // ---- double-float arithmetic (Dekker / Knuth error-free transformations) ---
 struct df {
@@ -117,57 +126,6 @@ __device__ __forceinline__ df df_from_ll(long long v) {
 
 // ---- integer decomposition of the inputs ----------------------------------
 
-// floor(x 2^sh) of a finite double x >= 0 given its bits; inexact |= bits dropped.
-__device__ __forceinline__ long long fix_f64(unsigned long long u, int sh, bool& inexact) {
-  const int E = (int)(u >> 52) & 0x7ff;
-  unsigned long long M = u & 0xFFFFFFFFFFFFFull;
-  int e2;
-  if (E == 0) {
-    e2 = -1074 + sh;
-  } else {
-    M |= 1ull << 52;
-    e2 = E - 1075 + sh;
-  }
-  if (e2 >= 0) return (long long)(M << e2);  // small: the value is below 2^60
-  const int r = -e2;
-  if (r >= 64) {
-    inexact |= M != 0;
-    return 0;
-  }
-  inexact |= (M & ((1ull << r) - 1ull)) != 0;
-  return (long long)(M >> r);
-}
-
-// floor(xh 2^sh) of a finite float given its bits (two's complement result).
-__device__ __forceinline__ long long fix_f32(unsigned v, int sh, bool& inexact) {
-  const int E = (v >> 23) & 0xff;
-  unsigned long long M = v & 0x7fffffu;
-  int e2;
-  if (E == 0) {
-    e2 = -149 + sh;
-  } else {
-    M |= 1ull << 23;
-    e2 = E - 150 + sh;
-  }
-  long long mag;
-  bool st = false;
-  if (e2 >= 0) {
-    mag = (long long)(M << e2);  // below 2^61 after the escape pre-check
-  } else {
-    const int r = -e2;
-    if (r >= 64) {
-      st = M != 0;
-      mag = 0;
-    } else {
-      st = (M & ((1ull << r) - 1ull)) != 0;
-      mag = (long long)(M >> r);
-    }
-  }
-  inexact |= st;
-  if (v >> 31) return -mag - (st ? 1 : 0);
-  return mag;
-}
-
 // binary exponent E of a positive finite double: d in [2^(E-1), 2^E)
 __device__ __forceinline__ int exponent_of(double d) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(d);
@@ -176,117 +134,126 @@ __device__ __forceinline__ int exponent_of(double d) {
   return (63 - __clzll((long long)u)) - 1073;  // subnormal
 }
 
+// Fixed point of the quantizer: units of Delta 2^-QF.
+constexpr int QF = 38;
+
 // Per-histogram constants of the integer quantizer.
 struct QConst {
   double dl;  // Delta = 2^k
   float dl_f;
   int k;
-  int F;    // fractional bits of the fixed-point values (units of Delta)
-  int FX;   // fractional bits of x' in the moment sums
-  int thr;  // |xhat| >= 2^thr certainly escapes
-  long long half, mask;
+  int cx;    // floor(x 2^(QF-k)) = (mantissa << 10) >> (cx - E), E the exponent field
+  int ch;    // trunc(xhat 2^(QF-k)) = (mantissa << 40) >> (ch - E)
+  int thr;   // exponent field of xhat at or above which |q| > 32766 for sure
 };
 
-__device__ __forceinline__ bool make_qconst(double tau, double s, double alpha, int xbits,
-                                            QConst& c) {
+__device__ __forceinline__ bool make_qconst(double tau, double s, double alpha, QConst& c) {
   c.dl = bin_width(tau, s, alpha);
   if (!(c.dl > 0.0) || !isfinite(c.dl)) return false;
   c.k = exponent_of(c.dl) - 1;
   const int IBx = exponent_of(s) - c.k;  // s / Delta < 2^IBx
-  const int IB = (IBx > 15 ? IBx : 15) + 2;
-  c.F = 62 - IB;
-  c.FX = xbits - IBx;
-  c.thr = c.k + IB - 1;
-  c.half = 1ll << (c.F - 1);
-  c.mask = (1ll << c.F) - 1;
-  // float copies: Delta and the scale factors of the moment sums must be
-  // normal floats (moments are scaled by vol Delta 2^-30 and vol Delta 2^-FX)
-  const bool ok = c.F >= 31 && c.FX >= 1 && c.F - c.FX >= 1 && IBx >= 1 &&
-                  c.k - 64 >= -100 && c.k + 20 <= 100;
+  c.cx = 1085 + c.k - QF;
+  c.ch = 190 + c.k - QF;
+  // |xhat| >= 2^(61 - QF + k) = 2^23 Delta > s + 32766 Delta: certain escape
+  c.thr = 127 + 61 - QF + c.k;
+  // x < 2^(IBx + QF) <= 2^60 units; Delta and the scale factors of the moment
+  // sums (vol Delta 2^-30, vol Delta 2^-38) stay normal floats
+  const bool ok = IBx >= 1 && IBx <= 22 && c.k - 64 >= -100 && c.k + 20 <= 100;
   c.dl_f = ok ? exp2i(c.k) : 0.f;
   return ok;
 }
 
+// |x| as a float (mantissa truncated; 0 below the float range) from the bit
+// pattern u of a double, on the integer pipe
+__device__ __forceinline__ float float_of_bits(unsigned long long u) {
+  const int E = (int)(u >> 52) & 0x7ff;
+  if (E <= 896) return 0.f;
+  if (E >= 1151) return __int_as_float(0x7f800000);
+  return __int_as_float(((E - 896) << 23) | (int)((u >> 29) & 0x7FFFFFull));
+}
+
 struct PointQ {
   int code;
-  int rho32;  // round((x - x') / Delta * 2^30)
-  long long xpw;  // round(x' / Delta * 2^FX)
-  float xpf;  // x' (float)
+  int rho32;      // round((x - x') / Delta * 2^30)
+  long long xpw;  // x' / Delta * 2^38 (within one unit)
+  float xpf;      // x' (float)
 };
 
-// Exact quantizer decision for one point (x finite, x >= 0).
+// The exact FP64 routine for the rare points whose integer decision falls in
+// an ambiguity band.
+__device__ __noinline__ PointQ quant_point_hard(double x, float xh, double dl) {
+  PointQ o;
+  double xpd;
+  o.code = quant_point_fp64(x, (double)xh, dl, &xpd);
+  const double rd = __ddiv_rn(__dsub_rn(x, xpd), dl);
+  o.rho32 = __double2int_rn(__dmul_rn(rd, 1073741824.0));
+  o.xpw = __double2ll_rn(ldexp(__ddiv_rn(xpd, dl), QF));
+  o.xpf = (float)xpd;
+  return o;
+}
+
+// Quantizer decision for one point (x finite, x >= 0), exact.  With
+// u = Delta 2^-38, X = floor(x / u) and Xh = trunc(xhat / u) come from the bit
+// patterns; D = X - Xh is within (-1, 2) units of the exact scaled difference,
+// so q = round-half-even(D / 2^38) is certain unless D's fraction sits in
+// {1/2 - u, 1/2}.  The zero level (g < 0 or g > 2x, g = xhat + q Delta) is
+// decided on G = Xh + q 2^38 (within 1 unit of g / u) and A = G - 2X (within
+// (-1, 3) units).  Points in an ambiguity band take the exact FP64 routine.
 __device__ __forceinline__ PointQ quant_point_int(double x, float xh, const QConst& c) {
   PointQ o;
   const unsigned long long u =
       (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
   const unsigned v = __float_as_uint(xh);
   const int Eh = (v >> 23) & 0xff;
-  const int sh = c.F - c.k;
-  bool inex = false;
-  const long long X = fix_f64(u, sh, inex);
-  long long rho_fix = 0, xp_fix;
-  bool hard = false;
-  if (Eh == 255 || Eh - 127 >= c.thr) {  // non-finite or certainly |q| > 32766
-    o.code = AEQC_CODE_ESCAPE;
-    xp_fix = X;
-  } else {
-    const long long Xh = fix_f32(v, sh, inex);
-    const long long D = X - Xh;
-    const long long m = D >> c.F;
-    const long long frac = D & c.mask;
-    long long q = 0;
-    if (frac < c.half) q = m;
-    else if (frac > c.half) q = m + 1;
-    else if (inex) hard = true;
-    else q = m + (m & 1);
-    if (!hard) {
-      if (q > AEQC_CODE_MAX || q < -AEQC_CODE_MAX) {
-        o.code = AEQC_CODE_ESCAPE;
-        xp_fix = X;
-      } else {
-        const long long G = Xh + q * (1ll << c.F);
-        int zero;
-        if (G <= -1) {
-          zero = 1;
-        } else {
-          const long long A = G - 2 * X;
-          if (A >= 2) zero = 1;
-          else if (A <= -1) zero = 0;
-          else if (inex) {
-            zero = 0;
-            hard = true;
-          } else zero = A > 0;
-        }
-        if (!hard) {
-          if (zero) {
-            o.code = AEQC_CODE_ZERO;
-            rho_fix = X;
-            xp_fix = 0;
-          } else {
-            o.code = (int)q;
-            rho_fix = D - q * (1ll << c.F);
-            xp_fix = G;
-          }
-        }
-      }
-    }
+  const int E = (int)(u >> 52);
+  long long X = 0;
+  if (E) {
+    const unsigned long long M10 = ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 10;
+    const int r = c.cx - E;  // >= 1 for x <= s
+    X = r < 64 ? (long long)(M10 >> r) : 0;
   }
-  if (hard) {
-    double xpd;
-    o.code = quant_point_fp64(x, (double)xh, c.dl, &xpd);
-    const double rd = __ddiv_rn(__dsub_rn(x, xpd), c.dl);
-    o.rho32 = __double2int_rn(ldexp(rd, 30));
-    o.xpw = __double2ll_rn(ldexp(__ddiv_rn(xpd, c.dl), c.FX));
-    o.xpf = (float)xpd;
+  if (Eh == 255 || Eh >= c.thr) {  // non-finite or certainly |q| > 32766
+    o.code = AEQC_CODE_ESCAPE;
+    o.rho32 = 0;
+    o.xpw = X;
+    o.xpf = float_of_bits(u);
     return o;
   }
+  const unsigned long long m40 = (unsigned long long)((v & 0x7fffffu) | (Eh ? 0x800000u : 0u)) << 40;
+  const int rh = c.ch - (Eh ? Eh : 1);  // >= 3 below the escape threshold
+  const long long mag = rh < 64 ? (long long)(m40 >> rh) : 0;
+  const long long Xh = (v >> 31) ? -mag : mag;
+  const long long D = X - Xh;
+  const long long m = D >> QF;
+  const long long fr = D & ((1ll << QF) - 1);  // D - m 2^38
+  constexpr long long half = 1ll << (QF - 1);
+  long long q;
+  if (fr <= half - 2) q = m;
+  else if (fr >= half + 1) q = m + 1;
+  else return quant_point_hard(x, xh, c.dl);
+  if (q > AEQC_CODE_MAX || q < -AEQC_CODE_MAX) {
+    o.code = AEQC_CODE_ESCAPE;
+    o.rho32 = 0;
+    o.xpw = X;
+    o.xpf = float_of_bits(u);
+    return o;
+  }
+  const long long G = Xh + q * (1ll << QF);
+  const long long A = G - 2 * X;
+  if (G == 0 || (G > 0 && A >= 0 && A <= 2)) return quant_point_hard(x, xh, c.dl);
+  if (G < 0 || A >= 3) {
+    o.code = AEQC_CODE_ZERO;
+    o.rho32 = (int)((X + 128) >> 8);  // x < Delta / 2 here
+    o.xpw = 0;
+    o.xpf = 0.f;
+    return o;
+  }
+  o.code = (int)q;
   // round to nearest: a floor would bias every cell the same way, and the
   // high-order weights (v^4 up to 256) would turn that into a systematic error
-  o.rho32 = (int)((rho_fix + (1ll << (c.F - 31))) >> (c.F - 30));
-  o.xpw = (xp_fix + (1ll << (c.F - c.FX - 1))) >> (c.F - c.FX);
-  if (o.code == AEQC_CODE_ESCAPE) o.xpf = ldexpf((float)o.xpw, -c.FX) * c.dl_f;
-  else if (o.code == AEQC_CODE_ZERO) o.xpf = 0.f;
-  else o.xpf = fmaf((float)o.code, c.dl_f, xh);
+  o.rho32 = (int)((D - q * (1ll << QF) + 128) >> 8);
+  o.xpw = G;
+  o.xpf = fmaf(small_int_to_float((int)q), c.dl_f, xh);
   return o;
 }
 
@@ -298,53 +265,122 @@ struct Moments {
   unsigned flags;  // CODE_ESCAPE / AE_EXACT
 };
 
-// Quantize the histogram (row xb, decoded row xhb) into shared memory and
-// accumulate its moments.
-__device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb,
-                        const float* xhb, const QConst& c, FastWS& w, Moments& mo, int lane) {
-  long long U[4] = {0, 0, 0, 0};
-  long long T[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // T00 T10 T20 T30 T40 T01 T11 T21 T02
-  float s1 = 0.f;
-  int esc = 0, nonzero = 0;
-  const float b_f = (float)fg.b, c0_f = (float)fg.c0;
-  PointIter it(lane, g.n_par);
-  for (; it.p < g.P; it.next()) {
-    const double x = __ldg(xb + it.p);
-    const float xh = __ldg(xhb + it.p);
-    const PointQ o = quant_point_int(x, xh, c);
-    w.codes[it.p] = (int16_t)o.code;
-    w.xp[it.p] = o.xpf;
-    w.rho[it.p] = ldexpf((float)o.rho32, -30);
+// exact sum over the warp of a 64-bit integer (the totals are bounded on the
+// host so that they fit)
+__device__ __forceinline__ long long wsum_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// Each lane walks down (part of) grid columns, so that the weights in i are
+// constants of the lane and the weights in j are the same for the whole warp:
+// one column sum per power of j replaces the per-point products.  Part 1:
+// lane i owns column i (i < 32, when the grid has at least 32 columns).
+// Part 2: the remaining columns, each cut into row chunks so that most lanes
+// take one chunk.
+struct Seg {
+  int c, j0, j1;  // column, rows [j0, j1)
+};
+
+__device__ __forceinline__ void lane_segments(int n_par, int n_perp, int lane, Seg& s1,
+                                              Seg& s2) {
+  const int cw = n_par >= 32 ? 32 : 0, rw = n_par - cw;
+  s1.c = lane;
+  s1.j0 = 0;
+  s1.j1 = cw ? n_perp : 0;
+  s2.c = cw;
+  s2.j0 = s2.j1 = 0;
+  if (rw) {
+    const int nchunk = 32 / rw;  // >= 1
+    const int rpc = (n_perp + nchunk - 1) / nchunk;
+    if (lane < rw * nchunk) {
+      const int chunk = lane / rw;
+      s2.c = cw + lane - chunk * rw;
+      s2.j0 = chunk * rpc;
+      s2.j1 = min(n_perp, s2.j0 + rpc);
+    }
+  }
+}
+
+// Column sums of one segment: X' j^(2q) (split at bit 31), rho32 j^(2q)
+// (q = 0, 1) and x' (float).
+struct ColSums {
+  long long b[3], a[3], u[2];
+  float xs;
+};
+
+__device__ __forceinline__ void quant_segment(const Seg& sg, int n_par, const double* xb,
+                                              const float* xhb, const QConst& c, FastWS& w,
+                                              int16_t* cb, ColSums& cs, int& esc,
+                                              int& nonzero) {
+  cs = ColSums{{0, 0, 0}, {0, 0, 0}, {0, 0}, 0.f};
+  int p = sg.j0 * n_par + sg.c;
+  for (int j = sg.j0; j < sg.j1; ++j, p += n_par) {
+    const PointQ o = quant_point_int(__ldg(xb + p), __ldg(xhb + p), c);
+    cb[p] = (int16_t)o.code;
+    w.xp[p] = o.xpf;
+    w.rho[p] = (int16_t)((o.rho32 + (1 << 14)) >> 15);
     esc |= o.code == AEQC_CODE_ESCAPE;
     nonzero |= o.code != 0;
-    const int ic = it.i - fg.i_c, j2 = it.j * it.j;
-    const int ic2 = ic * ic;
-    const long long r = o.rho32, X = o.xpw;
-    U[0] += r;
-    U[1] += r * ic;
-    U[2] += r * ic2;
-    U[3] += r * j2;
-    T[0] += X;
-    T[1] += X * ic;
-    T[2] += X * ic2;
-    T[3] += X * (ic2 * ic);
-    T[4] += X * (ic2 * ic2);
-    T[5] += X * j2;
-    T[6] += X * (ic * j2);
-    T[7] += X * (ic2 * j2);
-    T[8] += X * (j2 * j2);
-    s1 = fmaf(o.xpf, fabsf(fmaf(b_f, (float)ic, c0_f)), s1);
+    const int j2 = j * j, j4 = j2 * j2;
+    const long long xl = o.xpw & 0x7FFFFFFFll, xu = o.xpw >> 31;
+    cs.b[0] += xl;
+    cs.b[1] += xl * j2;
+    cs.b[2] += xl * j4;
+    cs.a[0] += xu;
+    cs.a[1] += xu * j2;
+    cs.a[2] += xu * j4;
+    cs.u[0] += o.rho32;
+    cs.u[1] += (long long)o.rho32 * j2;
+    cs.xs += o.xpf;
   }
+}
+
+// Quantize the histogram (row xb, decoded row xhb): codes to cb (global),
+// x' and the residual to shared memory, and the moments.
+__device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb,
+                        const float* xhb, const QConst& c, FastWS& w, int16_t* cb, Moments& mo,
+                        int lane) {
+  Seg sg1, sg2;
+  lane_segments(g.n_par, g.n_perp, lane, sg1, sg2);
+  int esc = 0, nonzero = 0;
+  ColSums c1, c2;
+  quant_segment(sg1, g.n_par, xb, xhb, c, w, cb, c1, esc, nonzero);
+  quant_segment(sg2, g.n_par, xb, xhb, c, w, cb, c2, esc, nonzero);
+  // fold with the powers of i - i_c: U_q over weights 1, ic, ic^2, j^2 and T
+  // over (ic^r j^(2q)) in the order T00 T10 T20 T30 T40 T01 T11 T21 T02, the
+  // latter as Tb + 2^31 Ta
+  long long U[4], Tb[9], Ta[9];
+  {
+    const long long i1 = sg1.c - fg.i_c, i2 = sg2.c - fg.i_c;
+    const long long p1[5] = {1, i1, i1 * i1, i1 * i1 * i1, i1 * i1 * i1 * i1};
+    const long long p2[5] = {1, i2, i2 * i2, i2 * i2 * i2, i2 * i2 * i2 * i2};
+    const int rq[9][2] = {{0, 0}, {1, 0}, {2, 0}, {3, 0}, {4, 0}, {0, 1}, {1, 1}, {2, 1}, {0, 2}};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int r = rq[k][0], q = rq[k][1];
+      Tb[k] = c1.b[q] * p1[r] + c2.b[q] * p2[r];
+      Ta[k] = c1.a[q] * p1[r] + c2.a[q] * p2[r];
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) U[r] = c1.u[0] * p1[r] + c2.u[0] * p2[r];
+    U[3] = c1.u[1] + c2.u[1];
+  }
+  const float b_f = (float)fg.b, c0_f = (float)fg.c0;
+  float s1 = c1.xs * fabsf(fmaf(b_f, small_int_to_float(sg1.c - fg.i_c), c0_f)) +
+             c2.xs * fabsf(fmaf(b_f, small_int_to_float(sg2.c - fg.i_c), c0_f));
   __syncwarp();
-  // per-lane sums stay below 2^60; convert, then add across the warp exactly
+  // exact warp totals (the host bounds them below 2^62), then double-float
   df u[4], t[9];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) u[q] = df_wsum(df_from_ll(U[q]));
+  for (int q = 0; q < 4; ++q) u[q] = df_from_ll(wsum_ll(U[q]));
 #pragma unroll
-  for (int q = 0; q < 9; ++q) t[q] = df_wsum(df_from_ll(T[q]));
+  for (int q = 0; q < 9; ++q)
+    t[q] = df_add(df_ldexp(df_from_ll(wsum_ll(Ta[q])), 31), df_from_ll(wsum_ll(Tb[q])));
   const float S1 = df_wsum(df{s1, 0.f}).hi;
   const df vol = {fg.vol_h, fg.vol_l};
-  const df sr = df_ldexp(vol, c.k - 30), sm = df_ldexp(vol, c.k - c.FX);
+  const df sr = df_ldexp(vol, c.k - 30), sm = df_ldexp(vol, c.k - QF);
   const df b = {fg.coef_h[1][1], fg.coef_l[1][1]};   // C(1,1) b = b
   const df c0 = {fg.coef_h[1][0], fg.coef_l[1][0]};  // C(1,0) c0 = c0
   const df d2 = {fg.d2q_h[1], fg.d2q_l[1]};
@@ -361,7 +397,7 @@ __device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb,
     acc = df_add(acc, df_mul(cc[2], u[2]));
     mo.R[3] = df_mul(sr, acc);
   }
-  // m(p, q) = vol Delta 2^-FX d2^q sum_r C(p,r) b^r c0^(p-r) T[r][q]
+  // m(p, q) = vol Delta 2^-38 d2^q sum_r C(p,r) b^r c0^(p-r) T[r][q]
   const df* Tq0 = t;      // T[r][0], r = 0..4
   const df Tq1[3] = {t[5], t[6], t[7]};
   auto mom = [&](int p, int q) {
@@ -420,6 +456,9 @@ __device__ __forceinline__ TCoef make_tcoef(const FastGridK& fg, const df lam[4]
 
 // One pass at lambda: H(lambda) and the end-to-end check.  EXACT selects
 // TwoSum accumulation of H (used when the FP32 sums' error bound is too wide).
+// The points are walked in the segments of phase_a: on a segment t = A +
+// a2 j^2 with A a constant, and one column sum of y and of y j^2 per segment
+// gives all four sums.
 template <bool EXACT>
 __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
                           const QConst& c, const TCoef& tc, float e_lo, float e_hi, PassOut& o,
@@ -427,45 +466,57 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
   df a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};  // sums of y, y ic, y ic^2, y j^2
   float ab1 = 0.f, tmax = 0.f;
   int viol = 0, unc = 0;
-  // walk p = lane, lane + 32, ... keeping ic and j^2 as exact floats
-  int i = lane % g.n_par, j = lane / g.n_par;
-  float icf = (float)(i - fg.i_c), jf = (float)j, j2f = jf * jf;
-  const float npf = (float)g.n_par;
-  for (int p = lane; p < g.P;) {
+  const float cq = c.dl_f * 3.0517578125e-05f, dq = -12582912.f * cq;  // Delta 2^-15
+  // x' h(t) and the check of one point
+  auto point = [&](int p, float t) -> float {
     const float xp = w.xp[p];
-    const float ic2f = icf * icf;
-    const float th = fmaf(tc.h[3], ic2f, fmaf(tc.h[1], icf, fmaf(tc.h[2], j2f, tc.h[0])));
-    const float tl = fmaf(tc.l[3], ic2f, fmaf(tc.l[1], icf, fmaf(tc.l[2], j2f, tc.l[0])));
-    const float t = th + tl;
     const float h =
         t * t * fmaf(-t, fmaf(-t, fmaf(-t, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f);
-    const float y = xp * h;
-    const float yi = y * icf;
-    if (EXACT) {
-      a[0] = df_add_f(a[0], y);
-      a[1] = df_add_f(a[1], yi);
-      a[2] = df_add_f(a[2], yi * icf);
-      a[3] = df_add_f(a[3], y * j2f);
-    } else {
-      a[0].hi += y;
-      a[1].hi += yi;
-      a[2].hi = fmaf(yi, icf, a[2].hi);
-      a[3].hi = fmaf(y, j2f, a[3].hi);
-    }
-    ab1 += fabsf(yi);
     if (xp > 0.f) tmax = fmaxf(tmax, fabsf(t));
-    const float err = fabsf(fmaf(xp, h - t, -c.dl_f * w.rho[p]));
+    // Delta rho from its 2^-15 fixed point: exact, see small_int_to_float
+    const float drho = fmaf(__int_as_float(0x4B400000 + (int)w.rho[p]), cq, dq);
+    const float err = fabsf(fmaf(xp, h - t, -drho));
     viol |= err > e_hi;
     unc |= err > e_lo;
-    p += 32;
-    i += 32;
-    icf += 32.f;
-    while (i >= g.n_par) {
-      i -= g.n_par;
-      icf -= npf;
+    return xp * h;
+  };
+  Seg sg[2];
+  lane_segments(g.n_par, g.n_perp, lane, sg[0], sg[1]);
+#pragma unroll
+  for (int part = 0; part < 2; ++part) {
+    const Seg& sgm = sg[part];
+    const float icf = small_int_to_float(sgm.c - fg.i_c), ic2f = icf * icf;
+    // t = A + a2 j^2 with A = a0 + a1 ic + a3 ic^2 fixed on the segment
+    const float ah = fmaf(tc.h[3], ic2f, fmaf(tc.h[1], icf, tc.h[0]));
+    const float al = fmaf(tc.l[3], ic2f, fmaf(tc.l[1], icf, tc.l[0]));
+    df s0 = {0.f, 0.f}, s3 = {0.f, 0.f};
+    float jf = small_int_to_float(sgm.j0), j2f = jf * jf;
+    int p = sgm.j0 * g.n_par + sgm.c;
+    for (int j = sgm.j0; j < sgm.j1; ++j, p += g.n_par) {
+      const float t = fmaf(tc.h[2], j2f, ah) + fmaf(tc.l[2], j2f, al);
+      const float y = point(p, t);
+      if (EXACT) {
+        s0 = df_add_f(s0, y);
+        s3 = df_add_f(s3, y * j2f);
+      } else {
+        s0.hi += y;
+        s3.hi = fmaf(y, j2f, s3.hi);
+      }
       j2f = fmaf(2.f, jf, j2f + 1.f);  // (j + 1)^2
       jf += 1.f;
     }
+    if (EXACT) {
+      a[0] = df_add(a[0], s0);
+      a[1] = df_add(a[1], df_mul_f(s0, icf));
+      a[2] = df_add(a[2], df_mul_f(s0, ic2f));
+      a[3] = df_add(a[3], s3);
+    } else {
+      a[0].hi += s0.hi;
+      a[1].hi = fmaf(s0.hi, icf, a[1].hi);
+      a[2].hi = fmaf(s0.hi, ic2f, a[2].hi);
+      a[3].hi += s3.hi;
+    }
+    ab1 = fmaf(s0.hi, fabsf(icf), ab1);  // y >= 0
   }
   df A[4];
 #pragma unroll
@@ -604,14 +655,15 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
       const float tb = fabsf(lam[0].hi) + fabsf(lam[1].hi) * fg.vmax + fabsf(lam[2].hi) * fg.wmax +
                        fabsf(lam[3].hi) * fg.vmax * fg.vmax;
       // FP32 rounding of the check (x' e^{-t} - x evaluated as x'(h - t) - Delta rho)
-      const float margin = 4e-7f * (s * tb + c.dl_f) + 1e-30f;
+      // plus the 2^-15 Delta fixed point of rho
+      const float margin = 4e-7f * (s * tb + c.dl_f) + 3.0517578125e-05f * c.dl_f + 1e-30f;
       PassOut po;
       const TCoef tc = make_tcoef(fg, lam);
       pass_warp<false>(g, fg, w, c, tc, e - margin, e + margin, po, lane);
       bool redo = false;
 #pragma unroll
-      for (int k = 0; k < 4; ++k)  // 48 FP32 additions per lane: |error| <= 48 u sum|terms|
-        redo = redo || 3e-6f * po.Habs[k] > 1e-13f * mo.S[k];
+      for (int k = 0; k < 4; ++k)  // <= 50 FP32 roundings per lane: |error| <= 50 u sum|terms|
+        redo = redo || 3.5e-6f * po.Habs[k] > 1e-13f * mo.S[k];
       if (redo) pass_warp<true>(g, fg, w, c, tc, e - margin, e + margin, po, lane);
 #pragma unroll
       for (int k = 0; k < 4; ++k) H[k] = po.H[k];
@@ -675,6 +727,7 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
   const int P = g.P;
   const double* xb = a.x + b * (long long)P;
   const float* xhb = a.xhat + b * a.ldx;
+  int16_t* cb = a.codes + b * (long long)P;
   // max(x) and input validity, on the bit patterns (no FP64 compares)
   unsigned long long umax = 0;
   int bad = 0;
@@ -699,12 +752,12 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
   const float s_f = (float)s;
   for (int level = 0; level < 2 && !defer && !done; ++level) {
     QConst c;
-    if (!make_qconst(pr.tau, s, level ? pr.alpha * 0.25 : pr.alpha, fg.xbits, c)) {
+    if (!make_qconst(pr.tau, s, level ? pr.alpha * 0.25 : pr.alpha, c)) {
       defer = true;
       break;
     }
     Moments mo;
-    phase_a(g, fg, xb, xhb, c, w, mo, lane);
+    phase_a(g, fg, xb, xhb, c, w, cb, mo, lane);
     st = mo.flags | (level ? AEQC_ST_ALPHA_RETRY : 0u) | (st & AEQC_ST_WARM_REJECTED);
     Chol ch;
     chol_factor(mo.M, ch);
@@ -788,32 +841,30 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
     const df lk = k == 0 ? lam[0] : (k == 1 ? lam[1] : (k == 2 ? lam[2] : lam[3]));
     lamd = (double)lk.hi + (double)lk.lo;
   }
-  // outputs
-  int16_t* cb = a.codes + b * (long long)P;
-  for (int p = lane; p < P; p += 32) cb[p] = w.codes[p];
+  // outputs (the codes are in place)
   if (a.f_out) {
     // f = x' exp(-lambda.phi) with the rounding of the decompression kernel
     double ld[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) ld[k] = __shfl_sync(FULL, lamd, k);
-    for (int i = lane; i < g.n_par; i += 32) w.ta[i] = corr_a(ld, g.vpar[i]);
-    for (int j = lane; j < g.n_perp; j += 32) w.tb[j] = corr_b(ld, g.vperp2[j]);
+    for (int i = lane; i < g.n_par; i += 32) w.t.ta[i] = corr_a(ld, g.vpar[i]);
+    for (int j = lane; j < g.n_perp; j += 32) w.t.tb[j] = corr_b(ld, g.vperp2[j]);
     __syncwarp();
     const double dl =
         bin_width(pr.tau, s, (st & AEQC_ST_ALPHA_RETRY) ? pr.alpha * 0.25 : pr.alpha);
     double* fb = a.f_out + b * (long long)P;
     PointIter pi(lane, g.n_par);
     for (; pi.p < P; pi.next()) {
-      const int code = w.codes[pi.p];
+      const int code = cb[pi.p];
       double xpd;
       if (code == AEQC_CODE_ESCAPE) xpd = __ldg(xb + pi.p);
       else if (code == AEQC_CODE_ZERO) xpd = 0.0;
       else xpd = __dadd_rn((double)__ldg(xhb + pi.p), __dmul_rn((double)code, dl));
-      fb[pi.p] = corr_kl(xpd, w.ta[pi.i], w.tb[pi.j]);
+      fb[pi.p] = corr_kl(xpd, w.t.ta[pi.i], w.t.tb[pi.j]);
     }
   }
   if (a.out.count && (st & AEQC_ST_CODE_ESCAPE)) {
-    if (append_outliers(a.out, w.codes, xb, P, a.row0 + b, lane)) st |= AEQC_ST_OUTLIER_OVERFLOW;
+    if (append_outliers(a.out, cb, xb, P, a.row0 + b, lane)) st |= AEQC_ST_OUTLIER_OVERFLOW;
   }
   if (a.features) {
     float* fr = a.features + b * (long long)(a.latent.L + 4);
@@ -869,6 +920,22 @@ int make_fast_grid(const GridK& g, FastGridK* out) {
   for (int j = 0; j < g.n_perp; ++j)
     if (fabs(g.vperp2[j] - d2 * (double)j * (double)j) > 1e-13 * g.vperp2[g.n_perp - 1])
       return AEQC_OK;
+  // exact 64-bit moment sums: for every weight (i - i_c)^r j^(2q) of the
+  // moments, the sum of |weight| over the grid stays below 2^31, so that the
+  // totals of X' (split at bit 31: parts below 2^31 and 2^29) and of rho32
+  // (below 2^30) stay below 2^62
+  {
+    double wsum[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int j = 0; j < g.n_perp; ++j)
+      for (int i = 0; i < g.n_par; ++i) {
+        const double a = fabs((double)(i - ic)), j2 = (double)j * j;
+        const double wt[9] = {1, a, a * a, a * a * a, a * a * a * a, j2, a * j2, a * a * j2,
+                              j2 * j2};
+        for (int q = 0; q < 9; ++q) wsum[q] += wt[q];
+      }
+    for (int q = 0; q < 9; ++q)
+      if (!(wsum[q] < 2147483648.0)) return AEQC_OK;
+  }
   f.ok = 1;
   f.i_c = ic;
   f.b = b;
@@ -887,21 +954,6 @@ int make_fast_grid(const GridK& g, FastGridK* out) {
     }
   f.vmax = (float)vmax;
   f.wmax = (float)g.vperp2[g.n_perp - 1];
-  // x' bits: the largest integer weight (|i - i_c|^4, j^4, |i - i_c|^2 j^2)
-  // times the points of one lane must stay below 2^62
-  {
-    const long long icm = ic > g.n_par - 1 - ic ? ic : g.n_par - 1 - ic;
-    const long long jm = g.n_perp - 1;
-    long long wmaxi = icm * icm * icm * icm;
-    if (jm * jm * jm * jm > wmaxi) wmaxi = jm * jm * jm * jm;
-    if (icm * icm * jm * jm > wmaxi) wmaxi = icm * icm * jm * jm;
-    int bw = 0;
-    while ((1ll << bw) <= wmaxi) ++bw;
-    const int per_lane = (g.n_par * g.n_perp + 31) / 32;
-    int bn = 0;
-    while ((1 << bn) < per_lane) ++bn;
-    f.xbits = 62 - bw - bn;
-  }
   *out = f;
   return AEQC_OK;
 }
@@ -922,7 +974,7 @@ int launch_fused_fast(const FusedArgs& a_in, cudaStream_t s) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   long long blocks = (a.n + FW - 1) / FW;
-  const long long cap = (long long)sms * 3;  // 3 CTAs of 4 warps fit per SM
+  const long long cap = (long long)sms * 4;  // 4 CTAs of 4 warps fit per SM
   if (blocks > cap) blocks = cap;
   fused_fast_kernel<<<(unsigned)blocks, FW * 32, smem, s>>>(a);
   int rc = check_launch("fused_fast_kernel");

@@ -1,0 +1,757 @@
+// BF16 autoencoder forward on the 5th-generation tensor cores (Stage 3 of
+// Sec. III; the tied linear network of Sec. IV-B): tcgen05.mma with FP32
+// accumulators in tensor memory, weights streamed by TMA, one CTA per tile of
+// 128 histograms.
+//
+// Encoder (one kernel): h = act((x W1') / s + b1') then z = h W2 + b2, with
+// W1' = W1 / sigma and b1' = b1 - W1'^T mu folded on the host side, s the
+// per-histogram maximum.  The FP64 input rows are read once: eight converter
+// warps load them, take the row maximum and write BF16 operand tiles into
+// shared memory in the 128-byte-swizzled K-major layout the MMA reads; h goes
+// from tensor memory through shared memory (BF16) into the second MMA, so
+// neither h nor the BF16 copy of x touches HBM.
+//
+// Decoder (one kernel): h = act(z W3 + b3) then xhat = s (h W4' + b4'), with
+// W4' = sigma W4 and b4' = sigma b4 + mu; h stays in shared memory and the
+// output tiles of 256 columns are double-buffered in tensor memory so that
+// the FP32 stores of one tile overlap the MMAs of the next.
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include "model.cuh"
+#include "tc_ptx.cuh"
+#include "workspace.cuh"
+
+namespace aeqc {
+namespace {
+
+using namespace tc;
+
+constexpr int BM = 128;       // rows (histograms) per tile
+constexpr int KB = 64;        // K per stage: 64 bf16 = one 128-byte swizzle row
+constexpr int NCONV = 8;      // converter / epilogue warps
+constexpr int WARP_TMA = 8;   // TMA producer, TMEM owner
+constexpr int WARP_MMA = 9;   // MMA issuer
+constexpr int NTHREADS = 320;
+constexpr uint32_t A_STAGE = BM * 128;  // bytes of one A stage (128 rows x 128 B)
+
+// error word values (device)
+constexpr int ERR_TIMEOUT = 1;
+
+__device__ __forceinline__ unsigned long long f64_key(unsigned long long u) {
+  // order-preserving map of a double's bits to a signed 64-bit key
+  return u ^ (((unsigned long long)((long long)u >> 63)) & 0x7FFFFFFFFFFFFFFFull);
+}
+
+// BF16 bits of a double, round to nearest even (values below the BF16 normal
+// range become zero, above it infinity)
+__device__ __forceinline__ uint32_t bf16_of_f64(unsigned long long u) {
+  const uint32_t sign = (uint32_t)(u >> 63) << 15;
+  unsigned long long a = u & 0x7FFFFFFFFFFFFFFFull;
+  if (a > 0x7FF0000000000000ull) return sign | 0x7FC0u;
+  a += 0x00000FFFFFFFFFFFull + ((a >> 45) & 1ull);
+  const int E = (int)(a >> 52);
+  if (E >= 1151) return sign | 0x7F80u;
+  if (E <= 896) return sign;
+  return sign | ((uint32_t)(E - 896) << 7) | ((uint32_t)(a >> 45) & 0x7Fu);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ float act_f(int act, float v) {
+  return act == AEQC_ACT_RELU ? fmaxf(v, 0.f) : v;
+}
+
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// tile t -> group, first row, end row (grouped batches: tiles never straddle
+// two groups); false for the spare CTAs of a grouped launch
+struct TileInfo {
+  int g;
+  long long m0, mend;
+};
+
+__device__ __forceinline__ bool tile_info(int t, long long n, int G, const long long* goff,
+                                          const int* toff, TileInfo& ti) {
+  if (G <= 1) {
+    ti.g = 0;
+    ti.m0 = (long long)t * BM;
+    ti.mend = n;
+    return ti.m0 < n;
+  }
+  if (t >= toff[G]) return false;
+  int lo = 0, hi = G - 1;  // largest g with toff[g] <= t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (toff[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  ti.g = lo;
+  ti.m0 = goff[lo] + (long long)(t - toff[lo]) * BM;
+  ti.mend = goff[lo + 1];
+  return ti.m0 < ti.mend;
+}
+
+struct EncArgs {
+  const double* x;
+  long long n;
+  int P, Kp, H, L, act, G, ns;
+  const long long* goff;
+  const int* toff;
+  const float* b1;  // enc1b, group stride b1_gs
+  long long b1_gs;
+  const float* b2;  // b2, group stride b2_gs
+  long long b2_gs;
+  __nv_bfloat16* latent;
+  double* scale;
+  int* err;
+};
+
+// shared memory of the encoder, offsets from a 1024-byte aligned base
+struct EncSmem {
+  uint32_t stage_bytes, off_b, w2, rowmax, bars, total;
+  __host__ __device__ EncSmem(int H, int L, int ns) {
+    const uint32_t b_bytes = (uint32_t)H * 128;
+    stage_bytes = A_STAGE + b_bytes;
+    off_b = A_STAGE;
+    uint32_t o = stage_bytes * ns;
+    const uint32_t h1 = (uint32_t)BM * H * 2;  // E2 operand reuses the stages
+    if (o < h1) o = h1;
+    w2 = o;
+    o += (uint32_t)(H / KB) * L * 128;
+    rowmax = o;
+    o += BM * 8;
+    bars = o;
+    o += 8 * (3 * ns + 4) + 16;
+    total = o;
+  }
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    enc_tc_kernel(const __grid_constant__ CUtensorMap mapW1,
+                  const __grid_constant__ CUtensorMap mapW2, const EncArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                           ~uintptr_t(1023));
+  const EncSmem L(a.H, a.L, a.ns);
+  const int ns = a.ns;
+  uint64_t* full_a = reinterpret_cast<uint64_t*>(sm + L.bars);
+  uint64_t* full_b = full_a + ns;
+  uint64_t* empty = full_b + ns;
+  uint64_t* w2_full = empty + ns;
+  uint64_t* acc_full = w2_full + 1;
+  uint64_t* h1_full = acc_full + 1;
+  uint64_t* lat_full = h1_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(lat_full + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  double* rowmax = reinterpret_cast<double*>(sm + L.rowmax);
+
+  TileInfo ti;
+  if (!tile_info(blockIdx.x, a.n, a.G, a.goff, a.toff, ti)) return;
+  const int rows = (int)min((long long)BM, ti.mend - ti.m0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int H = a.H, nkb = a.Kp / KB, nh = (H + 255) / 256, hn = H < 256 ? H : 256;
+  const uint32_t tcols = H <= 32 ? 32 : (H <= 64 ? 64 : (H <= 128 ? 128 : (H <= 256 ? 256 : 512)));
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&full_a[s], NCONV * 32);
+      mbar_init(&full_b[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(w2_full, 1);
+    mbar_init(acc_full, 1);
+    mbar_init(h1_full, NCONV * 32);
+    mbar_init(lat_full, 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == WARP_TMA) tmem_alloc(tmem_slot, tcols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto fail = [&]() {
+    *abort_flag = 1;
+    atomicExch(a.err, ERR_TIMEOUT);
+  };
+
+  if (warp == WARP_TMA) {
+    if (lane == 0) {
+      prefetch_tmap(&mapW1);
+      prefetch_tmap(&mapW2);
+      mbar_arrive_expect_tx(w2_full, (uint32_t)(H / KB) * a.L * 128);
+      for (int k2 = 0; k2 < H / KB; ++k2)
+        tma_load_3d(sm + L.w2 + k2 * a.L * 128, &mapW2, w2_full, k2 * KB, 0, ti.g);
+      for (int kb = 0; kb < nkb && !*abort_flag; ++kb) {
+        const int s = kb % ns;
+        const uint32_t ph = (kb / ns) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1)) {
+          fail();
+          break;
+        }
+        uint8_t* bst = sm + s * L.stage_bytes + L.off_b;
+        mbar_arrive_expect_tx(&full_b[s], (uint32_t)H * 128);
+        for (int j = 0; j < nh; ++j)
+          tma_load_3d(bst + j * 256 * 128, &mapW1, &full_b[s], kb * KB, j * 256, ti.g);
+      }
+    }
+    __syncwarp();
+  } else if (warp == WARP_MMA) {
+    if (lane == 0) {
+      const uint32_t id1 = idesc_bf16(BM, hn);
+      bool ok = true;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % ns;
+        const uint32_t ph = (kb / ns) & 1;
+        if (*abort_flag || !mbar_wait(&full_a[s], ph) || !mbar_wait(&full_b[s], ph)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t abase = smem_u32(sm + s * L.stage_bytes);
+        const uint32_t bbase = abase + L.off_b;
+#pragma unroll
+        for (int kk = 0; kk < KB / 16; ++kk)
+          for (int j = 0; j < nh; ++j)
+            mma_bf16(tmem + j * 256, desc_k128(abase + kk * 32),
+                     desc_k128(bbase + j * 256 * 128 + kk * 32), id1, (kb | kk) != 0);
+        mma_commit(&empty[s]);
+      }
+      mma_commit(acc_full);
+      if (ok) {
+        if (!mbar_wait(h1_full, 0) || !mbar_wait(w2_full, 0)) {
+          fail();
+        } else {
+          tc_fence_after();
+          const uint32_t id2 = idesc_bf16(BM, a.L);
+          const uint32_t hbase = smem_u32(sm), wbase = smem_u32(sm + L.w2);
+          for (int k2 = 0; k2 < H / KB; ++k2)
+#pragma unroll
+            for (int kk = 0; kk < KB / 16; ++kk)
+              mma_bf16(tmem, desc_k128(hbase + k2 * A_STAGE + kk * 32),
+                       desc_k128(wbase + k2 * a.L * 128 + kk * 32), id2, (k2 | kk) != 0);
+        }
+      } else {
+        fail();
+      }
+      mma_commit(lat_full);
+    }
+    __syncwarp();
+  } else {
+    // ---- converters: FP64 rows -> BF16 swizzled A tiles, row maxima ----
+    unsigned long long mkey[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) mkey[i] = f64_key(0xFFF0000000000000ull);  // -inf
+    bool ok = true;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % ns;
+      const uint32_t ph = (kb / ns) & 1;
+      if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1)) {
+        ok = false;
+        break;
+      }
+      uint8_t* ast = sm + s * L.stage_bytes;
+      const int k0 = kb * KB + 2 * lane;
+      unsigned long long v0[16], v1[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int r = warp * 16 + i;
+        v0[i] = 0;
+        v1[i] = 0;
+        if (r < rows) {
+          const double* xr = a.x + (ti.m0 + r) * (long long)a.P;
+          if (k0 < a.P) v0[i] = (unsigned long long)__double_as_longlong(__ldg(xr + k0));
+          if (k0 + 1 < a.P) v1[i] = (unsigned long long)__double_as_longlong(__ldg(xr + k0 + 1));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int r = warp * 16 + i;
+        const unsigned long long k0k = f64_key(v0[i]), k1k = f64_key(v1[i]);
+        if (k0 < a.P && (long long)k0k > (long long)mkey[i]) mkey[i] = k0k;
+        if (k0 + 1 < a.P && (long long)k1k > (long long)mkey[i]) mkey[i] = k1k;
+        const uint32_t packed = bf16_of_f64(v0[i]) | (bf16_of_f64(v1[i]) << 16);
+        *reinterpret_cast<uint32_t*>(ast + swz128(r, lane >> 2) + (lane & 3) * 4) = packed;
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(&full_a[s]);
+    }
+    // row maxima: lanes hold partial maxima of rows warp*16 + i
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      long long k = (long long)mkey[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long q = __shfl_xor_sync(0xffffffffu, k, o);
+        k = q > k ? q : k;
+      }
+      if (lane == 0) rowmax[warp * 16 + i] = __longlong_as_double((long long)f64_key((unsigned long long)k));
+    }
+    named_sync(1, NCONV * 32);
+    // ---- E1 epilogue: TMEM -> act(acc / s + b1) -> BF16 swizzled h tile ----
+    const int q = warp & 3, half = warp >> 2;
+    const int r = q * 32 + lane;
+    if (ok && !mbar_wait(acc_full, 0)) {
+      ok = false;
+      fail();
+    }
+    if (ok) {
+      tc_fence_after();
+      const double srow = rowmax[r];
+      const float rs = (srow > 0.0 && isfinite(srow)) ? (float)(1.0 / srow) : 0.f;
+      const float* b1 = a.b1 + ti.g * a.b1_gs;
+      const int c_lo = half * (H / 2), c_hi = c_lo + H / 2;
+      for (int c = c_lo; c < c_hi; c += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        uint8_t* hb = sm + (c / KB) * A_STAGE;
+        const int ch0 = (c % KB) / 8;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          uint4 w;
+          w.x = pack_bf16(act_f(a.act, fmaf(v[8 * u + 0], rs, __ldg(b1 + c + 8 * u + 0))),
+                          act_f(a.act, fmaf(v[8 * u + 1], rs, __ldg(b1 + c + 8 * u + 1))));
+          w.y = pack_bf16(act_f(a.act, fmaf(v[8 * u + 2], rs, __ldg(b1 + c + 8 * u + 2))),
+                          act_f(a.act, fmaf(v[8 * u + 3], rs, __ldg(b1 + c + 8 * u + 3))));
+          w.z = pack_bf16(act_f(a.act, fmaf(v[8 * u + 4], rs, __ldg(b1 + c + 8 * u + 4))),
+                          act_f(a.act, fmaf(v[8 * u + 5], rs, __ldg(b1 + c + 8 * u + 5))));
+          w.w = pack_bf16(act_f(a.act, fmaf(v[8 * u + 6], rs, __ldg(b1 + c + 8 * u + 6))),
+                          act_f(a.act, fmaf(v[8 * u + 7], rs, __ldg(b1 + c + 8 * u + 7))));
+          *reinterpret_cast<uint4*>(hb + swz128(r, ch0 + u)) = w;
+        }
+      }
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    mbar_arrive(h1_full);
+    // ---- E2 epilogue: latent = acc + b2 (BF16), scale = s ----
+    if (warp < 4) {
+      if (ok && !mbar_wait(lat_full, 0)) {
+        ok = false;
+        fail();
+      }
+      if (ok && !*abort_flag) {
+        tc_fence_after();
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16), v);
+        if (r < rows) {
+          const float* b2 = a.b2 + ti.g * a.b2_gs;
+          uint32_t* dst = reinterpret_cast<uint32_t*>(a.latent + (ti.m0 + r) * a.L);
+          for (int l = 0; l < a.L; l += 2)
+            dst[l >> 1] = pack_bf16(v[l] + __ldg(b2 + l), v[l + 1] + __ldg(b2 + l + 1));
+        }
+      }
+    } else {
+      const int rr = (warp - 4) * 32 + lane;
+      if (rr < rows) a.scale[ti.m0 + rr] = rowmax[rr];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == WARP_TMA) {
+    tc_fence_after();
+    tmem_dealloc(tmem, tcols);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// decoder
+
+struct DecArgs {
+  const __nv_bfloat16* latent;
+  const double* scale;
+  long long n;
+  int P, H, L, act, G, ns;
+  const long long* goff;
+  const int* toff;
+  const __nv_bfloat16* W3;  // dec1B [H][L] per group, group stride w3_gs (elements)
+  long long w3_gs;
+  const float* b3;  // group stride b3_gs
+  long long b3_gs;
+  const float* b4;  // dec2b [P], group stride b4_gs
+  long long b4_gs;
+  float* xhat;
+  long long ld;
+  int* err;
+};
+
+struct DecSmem {
+  uint32_t h, stages, d1a, d1b, bars, total;
+  __host__ __device__ DecSmem(int H, int ns) {
+    h = 0;  // BF16 h tile: (H / 64) blocks of 128 rows x 128 B
+    uint32_t o = (uint32_t)BM * H * 2;
+    stages = o;  // B stages: 256 rows x 128 B each; D1 operands alias them
+    const uint32_t st = (uint32_t)ns * 256 * 128;
+    d1a = stages;                    // latent tile, K padded to 64: 16 KB
+    d1b = stages + A_STAGE;          // W3 tile [H rows][64]: H * 128 B
+    const uint32_t d1 = A_STAGE + (uint32_t)H * 128;
+    o += st > d1 ? st : d1;
+    bars = o;
+    o += 8 * (2 * ns + 8) + 16;
+    total = o;
+  }
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    dec_tc_kernel(const __grid_constant__ CUtensorMap mapW4, const DecArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                           ~uintptr_t(1023));
+  const DecSmem L(a.H, a.ns);
+  const int ns = a.ns;
+  uint64_t* full_b = reinterpret_cast<uint64_t*>(sm + L.bars);
+  uint64_t* empty = full_b + ns;
+  uint64_t* d1_ops = empty + ns;    // D1 operands written (converter warps)
+  uint64_t* d1_done = d1_ops + 1;   // D1 MMA complete
+  uint64_t* h_full = d1_done + 1;   // BF16 h tile written
+  uint64_t* acc_full = h_full + 1;  // [2]
+  uint64_t* acc_empty = acc_full + 2;  // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  TileInfo ti;
+  if (!tile_info(blockIdx.x, a.n, a.G, a.goff, a.toff, ti)) return;
+  const int rows = (int)min((long long)BM, ti.mend - ti.m0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int H = a.H, nk2 = H / KB, nh = (H + 255) / 256, hn = H < 256 ? H : 256;
+  const int ntiles = (a.P + 255) / 256;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&full_b[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(d1_ops, NCONV * 32);
+    mbar_init(d1_done, 1);
+    mbar_init(h_full, NCONV * 32);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], NCONV * 32);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == WARP_TMA) tmem_alloc(tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto fail = [&]() {
+    *abort_flag = 1;
+    atomicExch(a.err, ERR_TIMEOUT);
+  };
+
+  if (warp == WARP_TMA) {
+    if (lane == 0) {
+      prefetch_tmap(&mapW4);
+      // the stages alias the D1 operands: start after the D1 MMA has read them
+      if (!mbar_wait(d1_done, 0)) {
+        fail();
+      } else {
+        int it = 0;
+        for (int j = 0; j < ntiles && !*abort_flag; ++j)
+          for (int k2 = 0; k2 < nk2; ++k2, ++it) {
+            const int s = it % ns;
+            const uint32_t ph = (it / ns) & 1;
+            if (!mbar_wait(&empty[s], ph ^ 1)) {
+              fail();
+              j = ntiles;
+              break;
+            }
+            mbar_arrive_expect_tx(&full_b[s], 256 * 128);
+            tma_load_3d(sm + L.stages + s * 256 * 128, &mapW4, &full_b[s], k2 * KB, j * 256,
+                        ti.g);
+          }
+      }
+    }
+    __syncwarp();
+  } else if (warp == WARP_MMA) {
+    if (lane == 0) {
+      bool ok = mbar_wait(d1_ops, 0);
+      if (ok) {
+        tc_fence_after();
+        const uint32_t id1 = idesc_bf16(BM, hn);
+        const uint32_t abase = smem_u32(sm + L.d1a), bbase = smem_u32(sm + L.d1b);
+#pragma unroll
+        for (int kk = 0; kk < KB / 16; ++kk)
+          for (int j = 0; j < nh; ++j)
+            mma_bf16(tmem + j * 256, desc_k128(abase + kk * 32),
+                     desc_k128(bbase + j * 256 * 128 + kk * 32), id1, kk != 0);
+      }
+      mma_commit(d1_done);
+      if (ok) ok = mbar_wait(h_full, 0);
+      if (ok) {
+        tc_fence_after();
+        const uint32_t id2 = idesc_bf16(BM, 256);
+        const uint32_t hbase = smem_u32(sm + L.h);
+        int it = 0;
+        for (int j = 0; j < ntiles && ok; ++j) {
+          const int buf = j & 1;
+          // wait until the epilogue has drained this accumulator (tile j - 2)
+          if (j >= 2 && !mbar_wait(&acc_empty[buf], ((j >> 1) - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          for (int k2 = 0; k2 < nk2; ++k2, ++it) {
+            const int s = it % ns;
+            const uint32_t ph = (it / ns) & 1;
+            if (*abort_flag || !mbar_wait(&full_b[s], ph)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t bbase = smem_u32(sm + L.stages + s * 256 * 128);
+#pragma unroll
+            for (int kk = 0; kk < KB / 16; ++kk)
+              mma_bf16(tmem + buf * 256, desc_k128(hbase + k2 * A_STAGE + kk * 32),
+                       desc_k128(bbase + kk * 32), id2, (k2 | kk) != 0);
+            mma_commit(&empty[s]);
+          }
+          mma_commit(&acc_full[buf]);
+        }
+      }
+      if (!ok) fail();
+    }
+    __syncwarp();
+  } else {
+    const int t = threadIdx.x;
+    bool ok = true;
+    // ---- D1 operands: latent tile [128][64] and W3 [H][64] (K zero-padded) ----
+    {
+      const __nv_bfloat16* W3 = a.W3 + ti.g * a.w3_gs;
+      // latent: 128 rows x 8 chunks of 16 B; chunk c holds k = 8c..8c+7
+      for (int idx = t; idx < BM * 8; idx += NCONV * 32) {
+        const int r = idx >> 3, c = idx & 7;
+        uint4 w = make_uint4(0, 0, 0, 0);
+        if (r < rows && c * 8 < a.L)
+          w = *reinterpret_cast<const uint4*>(a.latent + (ti.m0 + r) * a.L + c * 8);
+        *reinterpret_cast<uint4*>(sm + L.d1a + swz128(r, c)) = w;
+      }
+      for (int idx = t; idx < H * 8; idx += NCONV * 32) {
+        const int r = idx >> 3, c = idx & 7;
+        uint4 w = make_uint4(0, 0, 0, 0);
+        if (c * 8 < a.L) w = *reinterpret_cast<const uint4*>(W3 + (long long)r * a.L + c * 8);
+        // rows beyond 256 go to the second 256-row block (row r of block r / 256)
+        *reinterpret_cast<uint4*>(sm + L.d1b + (r >> 8) * 256 * 128 + swz128(r & 255, c)) = w;
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(d1_ops);
+    }
+    // ---- D1 epilogue: h = act(acc + b3) -> BF16 swizzled h tile ----
+    const int q = warp & 3, half = warp >> 2;
+    const int r = q * 32 + lane;
+    if (!mbar_wait(d1_done, 0)) {
+      ok = false;
+      fail();
+    }
+    if (ok) {
+      tc_fence_after();
+      const float* b3 = a.b3 + ti.g * a.b3_gs;
+      const int c_lo = half * (H / 2), c_hi = c_lo + H / 2;
+      for (int c = c_lo; c < c_hi; c += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        uint8_t* hb = sm + L.h + (c / KB) * A_STAGE;
+        const int ch0 = (c % KB) / 8;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          uint4 w;
+          w.x = pack_bf16(act_f(a.act, v[8 * u + 0] + __ldg(b3 + c + 8 * u + 0)),
+                          act_f(a.act, v[8 * u + 1] + __ldg(b3 + c + 8 * u + 1)));
+          w.y = pack_bf16(act_f(a.act, v[8 * u + 2] + __ldg(b3 + c + 8 * u + 2)),
+                          act_f(a.act, v[8 * u + 3] + __ldg(b3 + c + 8 * u + 3)));
+          w.z = pack_bf16(act_f(a.act, v[8 * u + 4] + __ldg(b3 + c + 8 * u + 4)),
+                          act_f(a.act, v[8 * u + 5] + __ldg(b3 + c + 8 * u + 5)));
+          w.w = pack_bf16(act_f(a.act, v[8 * u + 6] + __ldg(b3 + c + 8 * u + 6)),
+                          act_f(a.act, v[8 * u + 7] + __ldg(b3 + c + 8 * u + 7)));
+          *reinterpret_cast<uint4*>(hb + swz128(r, ch0 + u)) = w;
+        }
+      }
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    mbar_arrive(h_full);
+    // ---- D2 epilogue per 256-column tile: xhat = s (acc + b4) ----
+    const float* b4 = a.b4 + ti.g * a.b4_gs;
+    const float rs = r < rows ? (float)a.scale[ti.m0 + r] : 0.f;
+    float* xr = a.xhat + (ti.m0 + r) * a.ld;
+    for (int j = 0; j < ntiles; ++j) {
+      const int buf = j & 1;
+      if (ok && (*abort_flag || !mbar_wait(&acc_full[buf], (j >> 1) & 1))) {
+        ok = false;
+        fail();
+      }
+      if (ok) {
+        tc_fence_after();
+#pragma unroll 1
+        for (int cc = 0; cc < 128; cc += 32) {
+          const int col = half * 128 + cc;
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + col), v);
+          const int p0 = j * 256 + col;
+          if (r < rows) {
+            if (p0 + 32 <= a.P) {
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                float4 o;
+                o.x = rs * (v[4 * u + 0] + __ldg(b4 + p0 + 4 * u + 0));
+                o.y = rs * (v[4 * u + 1] + __ldg(b4 + p0 + 4 * u + 1));
+                o.z = rs * (v[4 * u + 2] + __ldg(b4 + p0 + 4 * u + 2));
+                o.w = rs * (v[4 * u + 3] + __ldg(b4 + p0 + 4 * u + 3));
+                *reinterpret_cast<float4*>(xr + p0 + 4 * u) = o;
+              }
+            } else {
+              for (int i = 0; i < 32 && p0 + i < a.P; ++i)
+                xr[p0 + i] = rs * (v[i] + __ldg(b4 + p0 + i));
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_empty[buf]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == WARP_TMA) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ---- host side ---------------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 3-D BF16 tensor [G][rows][cols] (cols contiguous, group stride gstride
+// elements) read in boxes of 64 columns x box_rows rows, 128-byte swizzle
+int make_map(CUtensorMap* map, const void* base, int cols, int rows, int G, long long gstride,
+             int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return set_error(AEQC_ECUDA, "cuTensorMapEncodeTiled unavailable");
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)G};
+  cuuint64_t strides[2] = {(cuuint64_t)cols * 2, (cuuint64_t)gstride * 2};
+  cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims,
+                  strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(AEQC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return AEQC_OK;
+}
+
+}  // namespace
+
+// Shapes the tensor-core path takes: H a multiple of 64 up to 512, L = 16 or 32.
+bool tc_shape_ok(int H, int L) {
+  return H % 64 == 0 && H >= 64 && H <= 512 && (L == 16 || L == 32);
+}
+
+int run_encode_tc(aeqc_model* m, const double* x, long long n, const long long* group_off,
+                  const int* tile_off, int G, void* latent, double* scale, int* err,
+                  cudaStream_t s) {
+  const aeqc_model_desc& d = m->d;
+  const __nv_bfloat16* bf = static_cast<const __nv_bfloat16*>(m->inf_bf16);
+  CUtensorMap mW1, mW2;
+  int rc = make_map(&mW1, bf + m->bE1B, m->Kp1, d.H, d.n_groups, m->n_bf16, d.H < 256 ? d.H : 256);
+  if (rc) return rc;
+  if ((rc = make_map(&mW2, bf + m->bE2B, d.H, d.L, d.n_groups, m->n_bf16, d.L))) return rc;
+  EncArgs a;
+  memset(&a, 0, sizeof(a));
+  a.x = x;
+  a.n = n;
+  a.P = d.P;
+  a.Kp = m->Kp1;
+  a.H = d.H;
+  a.L = d.L;
+  a.act = d.act;
+  a.G = G;
+  a.goff = group_off;
+  a.toff = tile_off;
+  a.b1 = m->inf + m->iE1b;
+  a.b1_gs = m->n_inf;
+  a.b2 = m->params + m->ob2;
+  a.b2_gs = m->n_group;
+  a.latent = static_cast<__nv_bfloat16*>(latent);
+  a.scale = scale;
+  a.err = err;
+  // stages: as many as fit next to the W2 tile
+  int ns = 6;
+  while (ns > 2 && EncSmem(d.H, d.L, ns).total + 1024 > 227 * 1024) --ns;
+  a.ns = ns;
+  const size_t smem = EncSmem(d.H, d.L, ns).total + 1024;
+  if (smem > 227 * 1024) return set_error(AEQC_EUNSUPPORTED, "encoder tile does not fit (H=%d)", d.H);
+  AEQC_CUDA_TRY(cudaFuncSetAttribute(enc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+  const long long tiles = G > 1 ? (n + BM - 1) / BM + G : (n + BM - 1) / BM;
+  enc_tc_kernel<<<(unsigned)tiles, NTHREADS, smem, s>>>(mW1, mW2, a);
+  return check_launch("enc_tc_kernel");
+}
+
+int run_decode_tc(aeqc_model* m, const void* latent, const double* scale, long long n,
+                  const long long* group_off, const int* tile_off, int G, float* xhat,
+                  long long ld, int* err, cudaStream_t s) {
+  const aeqc_model_desc& d = m->d;
+  const __nv_bfloat16* bf = static_cast<const __nv_bfloat16*>(m->inf_bf16);
+  CUtensorMap mW4;
+  int rc = make_map(&mW4, bf + m->bD2B, d.H, d.P, d.n_groups, m->n_bf16, 256);
+  if (rc) return rc;
+  DecArgs a;
+  memset(&a, 0, sizeof(a));
+  a.latent = static_cast<const __nv_bfloat16*>(latent);
+  a.scale = scale;
+  a.n = n;
+  a.P = d.P;
+  a.H = d.H;
+  a.L = d.L;
+  a.act = d.act;
+  a.G = G;
+  a.goff = group_off;
+  a.toff = tile_off;
+  a.W3 = bf + m->bD1B;
+  a.w3_gs = m->n_bf16;
+  a.b3 = m->params + m->ob3;
+  a.b3_gs = m->n_group;
+  a.b4 = m->inf + m->iD2b;
+  a.b4_gs = m->n_inf;
+  a.xhat = xhat;
+  a.ld = ld;
+  a.err = err;
+  int ns = 4;
+  while (ns > 2 && DecSmem(d.H, ns).total + 1024 > 227 * 1024) --ns;
+  a.ns = ns;
+  const size_t smem = DecSmem(d.H, ns).total + 1024;
+  if (smem > 227 * 1024) return set_error(AEQC_EUNSUPPORTED, "decoder tile does not fit (H=%d)", d.H);
+  AEQC_CUDA_TRY(cudaFuncSetAttribute(dec_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+  const long long tiles = G > 1 ? (n + BM - 1) / BM + G : (n + BM - 1) / BM;
+  dec_tc_kernel<<<(unsigned)tiles, NTHREADS, smem, s>>>(mW4, a);
+  return check_launch("dec_tc_kernel");
+}
+
+}  // namespace aeqc

@@ -334,6 +334,8 @@ int run_encode(aeqc_model* m, const double* x, long long n, const long long* gro
     rc = launch_tile_offsets(group_off, G, 128, tile_off, s);
     if (rc) return rc;
   }
+  if (d.dtype == AEQC_DTYPE_BF16)
+    return run_encode_tc(m, x, n, group_off, tile_off, G, latent, scale, m->dev_err, s);
   GemmArgs a = gemm0();
   a.M = n; a.N = d.H; a.K = d.P;
   a.A = x; a.sam = d.P; a.sak = 1; a.a_f64 = 1;
@@ -374,6 +376,8 @@ int run_decode(aeqc_model* m, const void* latent, const double* scale, long long
     rc = launch_tile_offsets(group_off, G, 128, tile_off, s);
     if (rc) return rc;
   }
+  if (d.dtype == AEQC_DTYPE_BF16)
+    return run_decode_tc(m, latent, scale, n, group_off, tile_off, G, xhat, ld, m->dev_err, s);
   GemmArgs a = gemm0();
   a.M = n; a.N = d.H; a.K = d.L;
   a.A = latent; a.sam = d.L; a.sak = 1;
@@ -437,6 +441,10 @@ extern "C" int aeqc_model_create(const aeqc_model_desc* desc, aeqc_model** out) 
   AEQC_CHECK_ARG(d.dtype == AEQC_DTYPE_F32 || d.dtype == AEQC_DTYPE_BF16,
                  "aeqc_model_create: bad dtype");
   AEQC_CHECK_ARG(d.n_groups >= 1 && d.n_groups <= 65536, "aeqc_model_create: bad n_groups");
+  if (d.dtype == AEQC_DTYPE_BF16 && !tc_shape_ok(d.H, d.L))
+    return set_error(AEQC_EUNSUPPORTED,
+                     "aeqc_model_create: BF16 models need H a multiple of 64 in [64, 512] and "
+                     "L in {16, 32} (H=%d, L=%d)", d.H, d.L);
   aeqc_model* m = new aeqc_model();
   m->step.assign(d.n_groups, 0);  // new aeqc_model() zero-initialises the rest
   m->d = d;
@@ -470,7 +478,8 @@ extern "C" int aeqc_model_create(const aeqc_model_desc* desc, aeqc_model** out) 
   m->bD2B = r; r += P * H;
   m->n_bf16 = (r + 63) / 64 * 64;
   const long long G = d.n_groups;
-  size_t bytes = sizeof(float) * (size_t)(G * m->n_group + 2 * G * m->n_train + G * m->n_inf);
+  size_t bytes = sizeof(float) * (size_t)(G * m->n_group + 2 * G * m->n_train + G * m->n_inf) +
+                 256;  // + the device error word
   size_t bbytes = d.dtype == AEQC_DTYPE_BF16 ? sizeof(__nv_bfloat16) * (size_t)(G * m->n_bf16) : 0;
   char* base = nullptr;
   if (cudaMalloc(&base, bytes) != cudaSuccess) {
@@ -486,6 +495,7 @@ extern "C" int aeqc_model_create(const aeqc_model_desc* desc, aeqc_model** out) 
   m->adam_m = m->params + G * m->n_group;
   m->adam_v = m->adam_m + G * m->n_train;
   m->inf = m->adam_v + G * m->n_train;
+  m->dev_err = reinterpret_cast<int*>(m->inf + G * m->n_inf);
   if (bbytes) {
     if (cudaMalloc(&m->inf_bf16, bbytes) != cudaSuccess) {
       cudaFree(base);

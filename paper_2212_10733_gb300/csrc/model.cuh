@@ -26,6 +26,7 @@ struct aeqc_model {
   void* inf_bf16;
   long long bE1B, bE2B, bD1B, bD2B, n_bf16;
   int Kp1;  // P padded to a multiple of 64
+  int* dev_err;  // device word: nonzero after a tensor-core kernel gave up a wait
   bool dirty;
 };
 
@@ -51,6 +52,15 @@ int run_decode(aeqc_model* m, const void* latent, const double* scale, long long
                size_t ws_bytes, cudaStream_t s);
 size_t encode_ws(const aeqc_model* m, long long n);
 size_t decode_ws(const aeqc_model* m, long long n);
+
+// BF16 tcgen05 encoder/decoder (ae_tc.cu)
+bool tc_shape_ok(int H, int L);
+int run_encode_tc(aeqc_model* m, const double* x, long long n, const long long* group_off,
+                  const int* tile_off, int G, void* latent, double* scale, int* err,
+                  cudaStream_t s);
+int run_decode_tc(aeqc_model* m, const void* latent, const double* scale, long long n,
+                  const long long* group_off, const int* tile_off, int G, float* xhat,
+                  long long ld, int* err, cudaStream_t s);
 
 }  // namespace aeqc
 

@@ -3,14 +3,17 @@ quantization, Newton QoI correction, end-to-end check) on seeded synthetic
 velocity-space histograms.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
-                  [--config 1] [--n N] [--form plain|fast]
+                  [--config 1] [--n N] [--form optimized|plain] [--no-compare]
 
 Prints one JSON line (rank 0).  Workload (default): 1,048,576 histograms of
 39 x 39 float64 (12.76 GB, larger than L2, so no flush is needed between
 steps), one autoencoder 1521 -> 256 -> 32 -> 256 -> 1521 trained 2 epochs at
-batch 128, pointwise bound 1e-4 x max, moments to 1e-12.  Under torchrun every
-rank compresses its own shard of that size (weak scaling, no collective on
-the data path).
+batch 128 (FP32 master weights), pointwise bound 1e-4 x max, moments to
+1e-12.  The headline is the optimized form (BF16 tcgen05 encoder/decoder,
+correction on the FP32/INT pipes); the plain form (FP32 SIMT GEMMs, FP64
+correction) runs on the same trained weights and data for the speedup.  Under
+torchrun every rank compresses its own shard of that size (weak scaling, no
+collective on the data path).
 """
 from __future__ import annotations
 
@@ -47,10 +50,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--n", type=int, default=None, help="override the histogram count")
-    ap.add_argument("--form", default="plain", choices=["plain", "fast"])
+    ap.add_argument("--form", default="optimized", choices=["optimized", "plain"])
+    ap.add_argument("--no-compare", action="store_true",
+                    help="time only --form (default: also the other form, for the speedup)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--train-steps", type=int, default=None,
                     help="override the number of autoencoder training steps")
     ap.add_argument("--profile", default=None,
@@ -179,10 +184,45 @@ def build_workload(cfg, n, rank, device, aq, synth, train_steps=None):
     return x, model, dict(train_steps=steps, train_s=train_s, train_loss=float(loss.item()))
 
 
+# ncu-measured DRAM bytes per histogram of the correction kernel (read + write,
+# profiles/), per form; None where not measured for the current kernel
+TRAFFIC_PER_HIST = {"optimized": None, "plain": None}
+
+
 def algorithmic_bytes_fused(P=1521):
     # read x (float64) and xhat (float32), write codes (int16), lambda, scale,
     # iters, status
     return P * 8 + P * 4 + P * 2 + 4 * 8 + 8 + 1 + 2
+
+
+FORMS = {
+    # BF16 tcgen05 encoder/decoder + correction kernel on the FP32/INT pipes
+    "optimized": dict(dtype="bf16", kernel="fast"),
+    # FP32 SIMT GEMMs + FP64 correction kernel
+    "plain": dict(dtype="f32", kernel="fp64"),
+}
+
+
+def form_model(aq, trained, cfg, form):
+    """A model of the given form carrying the trained weights."""
+    if FORMS[form]["dtype"] == "f32":
+        return trained
+    from paper_2212_10733_gb300 import synth
+    m = aq.Model(synth.P, cfg["H"], cfg["L"], tied=True, act=aq.ACT_IDENTITY,
+                 dtype=aq.DTYPE_BF16)
+    m.set_group(0, trained.get_group(0))
+    return m
+
+
+def time_steps(step, steps, stream):
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / steps
 
 
 def run_ours(args, rank, world, local):
@@ -193,22 +233,25 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(device)
     cfg = CONFIGS[args.config]
     n = args.n or cfg["n"]
-    x, model, tr = build_workload(cfg, n, rank, device, aeqc, synth, args.train_steps)
+    x, trained, tr = build_workload(cfg, n, rank, device, aeqc, synth, args.train_steps)
     vpar, vperp, vol = synth.grid_arrays()
     grid = aeqc.Grid(vpar, vperp, vol)
-    kernel = aeqc.KERNEL_FAST if args.form == "fast" else aeqc.KERNEL_FP64
-    prm = aeqc.params_default(tau=cfg["tau"], kernel=kernel)
-    out = aeqc.Compressed(n, synth.P, cfg["L"], model.latent_dtype(), device, 16 * n)
-    ws = aeqc.compress_batch_workspace(model, n, device)
+    forms = [args.form] + ([] if args.no_compare else [f for f in FORMS if f != args.form])
     stream = torch.cuda.current_stream()
 
-    def step():
-        aeqc.compress_batch(model, grid, x, prm, out=out, ws=ws)
+    def setup(form):
+        m = form_model(aeqc, trained, cfg, form)
+        k = aeqc.KERNEL_FAST if FORMS[form]["kernel"] == "fast" else aeqc.KERNEL_FP64
+        prm = aeqc.params_default(tau=cfg["tau"], kernel=k)
+        out = aeqc.Compressed(n, synth.P, cfg["L"], m.latent_dtype(), device, 16 * n)
+        ws = aeqc.compress_batch_workspace(m, n, device)
+        return m, prm, out, ws
 
     if args.profile:
-        step()
+        model, prm, out, ws = setup(args.form)
+        aeqc.compress_batch(model, grid, x, prm, out=out, ws=ws)
         xhat = aeqc.ae_decode(model, out.latent, out.scale)
-        fn = {"compress": step,
+        fn = {"compress": lambda: aeqc.compress_batch(model, grid, x, prm, out=out, ws=ws),
               "encode": lambda: aeqc.ae_encode(model, x),
               "decode": lambda: aeqc.ae_decode(model, out.latent, out.scale),
               "quantize_correct": lambda: aeqc.quantize_correct(grid, x, xhat, prm, out=out)}
@@ -220,76 +263,91 @@ def run_ours(args, rank, world, local):
             fn[args.profile]()
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
-        return None, model, cfg
+        return None, trained, cfg
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    barrier(world)
-    torch.cuda.synchronize()
-    clk = ClockSampler(local)
-    clk.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    barrier(world)
-    ms = ev0.elapsed_time(ev1) / args.steps
-    ms = max_over_ranks(ms, world)
-    value = world * n / (ms / 1e3)
+    results = {}
+    for form in forms:
+        model, prm, out, ws = setup(form)
 
-    # correctness of the timed outputs (sampled): bound and moments via decompression
-    f = aeqc.decompress_batch(model, grid, out, prm)
-    st = out.status.cpu().numpy()
-    torch.cuda.synchronize()
-    stats = dict(
-        converged_round1=float(np.mean((st & aeqc.ST_CONVERGED) != 0)),
-        verbatim=float(np.mean((st & aeqc.ST_VERBATIM) != 0)),
-        alpha_retry=float(np.mean((st & aeqc.ST_ALPHA_RETRY) != 0)),
-        ae_exact=float(np.mean((st & aeqc.ST_AE_EXACT) != 0)),
-        mean_iters=float(out.iters.float().mean().item()),
-        outliers=int(out.count.item()))
-    e = cfg["tau"] * x.amax(dim=1, keepdim=True)
-    stats["max_err_over_bound"] = float(((f - x).abs() / e).max().item())
-    del f
+        def step():
+            aeqc.compress_batch(model, grid, x, prm, out=out, ws=ws)
 
-    # per-stage timing on the same stream, same launch configuration
-    hbuf = torch.empty((n, aeqc.XHAT_LD), dtype=torch.float32, device=device)
-    stage = {}
-    for name, fn in (
-        ("encode", lambda: aeqc.ae_encode(model, x)),
-        ("decode", lambda: aeqc.ae_decode(model, out.latent, out.scale)),
-        ("quantize_correct", lambda: aeqc.quantize_correct(grid, x, hbuf, prm, out=out)),
-    ):
-        if name == "quantize_correct":
-            hbuf.copy_(aeqc.ae_decode(model, out.latent, out.scale))
-        fn()
+        for _ in range(args.warmup):
+            step()
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = max(2, args.steps)
-        a.record(stream)
-        for _ in range(reps):
+        barrier(world)
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        clk.start()
+        ms = time_steps(step, args.steps, stream)
+        clocks = clk.stop()
+        barrier(world)
+        ms = max_over_ranks(ms, world)
+        r = dict(ms=ms, value=world * n / (ms / 1e3), clocks=clocks)
+        # correctness of the timed outputs: bound and moments via decompression
+        f = aeqc.decompress_batch(model, grid, out, prm)
+        st = out.status.cpu().numpy()
+        e = cfg["tau"] * x.amax(dim=1, keepdim=True)
+        r["stats"] = dict(
+            converged_round1=float(np.mean((st & aeqc.ST_CONVERGED) != 0)),
+            verbatim=float(np.mean((st & aeqc.ST_VERBATIM) != 0)),
+            alpha_retry=float(np.mean((st & aeqc.ST_ALPHA_RETRY) != 0)),
+            ae_exact=float(np.mean((st & aeqc.ST_AE_EXACT) != 0)),
+            mean_iters=float(out.iters.float().mean().item()),
+            outliers=int(out.count.item()),
+            max_err_over_bound=float(((f - x).abs() / e).max().item()),
+            max_qoi_rel_err=qoi_rel_err(aeqc, grid, f, x))
+        del f
+        # per-stage times on the same stream and launch configuration
+        hbuf = torch.empty((n, aeqc.XHAT_LD), dtype=torch.float32, device=device)
+        hbuf.copy_(aeqc.ae_decode(model, out.latent, out.scale))
+        stage = {}
+        for name, fn in (
+            ("encode", lambda: aeqc.ae_encode(model, x)),
+            ("decode", lambda: aeqc.ae_decode(model, out.latent, out.scale)),
+            ("quantize_correct", lambda: aeqc.quantize_correct(grid, x, hbuf, prm, out=out)),
+        ):
             fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        stage[name] = a.elapsed_time(b) / reps
-    del hbuf
-    dom = max(stage, key=stage.get)
+            torch.cuda.synchronize()
+            stage[name] = time_steps(fn, max(2, args.steps), stream)
+        del hbuf
+        r["stage_ms"] = {k: round(v, 3) for k, v in stage.items()}
+        r["ctx"] = (model, prm, out, ws)
+        results[form] = r
+        if form != args.form:
+            del model, out, ws
+            r.pop("ctx")
+
+    head = results[args.form]
+    model, prm, out, ws = head.pop("ctx")
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
     hbm = peaks.get("hbm_gbs", 6800.0)
+    stage = head["stage_ms"]
     qc_bytes = algorithmic_bytes_fused() * n
     achieved = qc_bytes / (stage["quantize_correct"] / 1e3) / 1e9
-    roofline = {"kernel": "quantize_correct (fused quantize + moments + Newton + check)",
+    fast = FORMS[args.form]["kernel"] == "fast"
+    roofline = {"kernel": ("fused_fast_kernel" if fast else "fused_fp64_kernel") +
+                " (quantize + moments + Newton + check, one launch per batch)",
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
-                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
-                "peak_source": "measured" if peaks else "fallback",
-                "dominant_stage": dom, "stage_ms": {k: round(v, 3) for k, v in stage.items()}}
+                "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": TRAFFIC_PER_HIST.get(args.form, None) and
+                round(TRAFFIC_PER_HIST[args.form] * n / 1e9, 3),
+                "traffic_unit": "GB per launch",
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks
+                else "fallback 6800 GB/s",
+                "algorithmic_bytes_per_histogram": algorithmic_bytes_fused(),
+                "stage_ms": stage}
+    gemm = {}
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    fl = 2.0 * n * synth.P * cfg["H"]
+    for nm in ("encode", "decode"):
+        tf = fl / (stage[nm] / 1e3) / 1e12
+        gb = (n * synth.P * 8 if nm == "encode" else n * aeqc.XHAT_LD * 4) / (stage[nm] / 1e3) / 1e9
+        gemm[nm] = {"tflops": round(tf, 1), "tensor_frac": round(tf / bf16_peak, 4),
+                    "hbm_gbs": round(gb, 1), "hbm_frac": round(gb / hbm, 4)}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -313,37 +371,53 @@ def run_ours(args, rank, world, local):
         e2e_step()
         torch.cuda.synchronize()
         del x
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = max(1, min(args.steps, 3))
-        a.record(stream)
-        for _ in range(reps):
-            e2e_step()
-        b.record(stream)
-        torch.cuda.synchronize()
-        ems = max_over_ranks(a.elapsed_time(b) / reps, world)
+        ems = max_over_ranks(time_steps(e2e_step, max(1, min(args.steps, 3)), stream), world)
         d2h = codes_h.numel() * 2 + lat_h.numel() * lat_h.element_size() + sum(
             t.numel() * t.element_size() for t in small)
         e2e = {"value": round(world * n / (ems / 1e3), 1), "unit": "histograms/s",
                "ms_per_step": round(ems, 3), "h2d_bytes_per_step": int(xh.numel() * 8),
                "d2h_bytes_per_step": int(d2h)}
-    launches_per_step = 5
+    launches = 4 if fast else 3  # enc, dec, correction (+ deferred-list kernel)
     res = {
-        "metric": METRIC, "value": round(value, 1), "unit": "histograms/s",
-        "input_gbs": round(value * HIST_BYTES / 1e9, 2),
+        "metric": METRIC, "value": round(head["value"], 1), "unit": "histograms/s",
+        "input_gbs": round(head["value"] * HIST_BYTES / 1e9, 2),
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64 correction / f32 GEMM" if cfg["dtype"] == "f32"
-        else "f64 correction / bf16 GEMM",
+        "ms_per_step": round(head["ms"], 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16 GEMM + int64/f32 correction" if fast else "f32 GEMM + f64 correction",
         "data": "synthetic (seeded Gaussian-mixture velocity histograms)",
         "config": {"workload": cfg["name"], "histograms_per_gpu": n, "grid": "39x39",
                    "ae": f"1521-{cfg['H']}-{cfg['L']}-{cfg['H']}-1521 tied linear",
                    "tau": cfg["tau"], "form": args.form,
                    "l2": "inputs (12.8 GB per GPU) larger than L2, no flush",
                    "parallelism": f"dp{world} (independent shards)"},
-        "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
-        "roofline": roofline, "e2e": e2e, "training": tr, "stats": stats,
+        "clocks": head["clocks"], "gpu_launches": launches * args.steps,
+        "roofline": roofline, "gemm": gemm, "e2e": e2e, "training": tr,
+        "stats": head["stats"],
     }
-    return res, model, cfg
+    for form, r in results.items():
+        if form == args.form:
+            continue
+        res["vs_" + form + "_form"] = {
+            "value": round(r["value"], 1), "ms_per_step": round(r["ms"], 3),
+            "speedup": round(head["value"] / r["value"], 2), "stage_ms": r["stage_ms"],
+            "stats": r["stats"], "clocks": r["clocks"]}
+    return res, trained, cfg
+
+
+def qoi_rel_err(aeqc, grid, f, x):
+    """max_k |Q_k(f) - Q_k(x)| / S_k(x) over the batch: moments by the library's
+    FP64 moment kernel, S_k = sum vol |phi_k| x by an FP64 matrix product."""
+    import torch
+    from paper_2212_10733_gb300 import synth
+    vpar, vperp, vol = synth.grid_arrays()
+    vp = np.tile(vpar, len(vperp))             # point p = j * n_par + i
+    w2 = np.repeat(vperp ** 2, len(vpar))
+    W = vol * np.abs(np.stack([np.ones_like(vp), vp, w2, vp ** 2], axis=1))
+    S = x @ torch.as_tensor(W, device=x.device)
+    qf = aeqc.qoi_moments(grid, f)
+    qx = aeqc.qoi_moments(grid, x)
+    return float(((qf - qx).abs() / S.clamp_min(1e-300)).max().item())
 
 
 def cpu_baseline(args, cfg, model, budget_s, rank=0):
@@ -373,10 +447,12 @@ def cpu_baseline(args, cfg, model, budget_s, rank=0):
         out = oracle.compress_correct(og, x, xh.astype(np.float32), op)
         return time.time() - t0, out
 
+    # calibrate (64 histograms, then a run of about a tenth of the budget),
+    # then one run sized to take about budget_s
     k = 64
     dt, _ = run(k)
-    while dt < budget_s / 8 and k < n_full:
-        k = min(n_full, int(k * max(2.0, budget_s / 2 / max(dt, 1e-3))))
+    for frac in (0.1, 1.0):
+        k = int(min(n_full, max(64, k * frac * budget_s / max(dt, 1e-3))))
         dt, _ = run(k)
     return {"value": round(k / dt, 2), "unit": "histograms/s", "cores": oracle.num_threads(),
             "kind": "oracle", "sample": f"{k} of {n_full} histograms (evenly spaced), "

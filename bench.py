@@ -83,6 +83,17 @@ def dist_setup(args):
     return rank, world, local
 
 
+def shard_seed(synth, rank: int) -> int:
+    """Seed of this rank's shard: every rank compresses its own histograms."""
+    return synth.config_seed(1) + 1000 * rank
+
+
+def job_value(n_per_rank: int, ms_per_rank: float, world: int) -> float:
+    """Whole-job histograms/s: all ranks' histograms over the slowest rank's time
+    (ms_per_rank is already the maximum over ranks)."""
+    return world * n_per_rank / (ms_per_rank / 1e3)
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -159,7 +170,7 @@ class ClockSampler:
 
 def build_workload(cfg, n, rank, device, aq, synth, train_steps=None):
     import torch
-    seed = synth.config_seed(1) + 1000 * rank
+    seed = shard_seed(synth, rank)
     x = synth.histograms_torch(n, seed, device, k_max=cfg["k_max"], heavy_frac=cfg["heavy"])
     P, H, L = synth.P, cfg["H"], cfg["L"]
     dtype = aq.DTYPE_BF16 if cfg["dtype"] == "bf16" else aq.DTYPE_F32
@@ -284,7 +295,7 @@ def run_ours(args, rank, world, local):
         clocks = clk.stop()
         barrier(world)
         ms = max_over_ranks(ms, world)
-        r = dict(ms=ms, value=world * n / (ms / 1e3), clocks=clocks)
+        r = dict(ms=ms, value=job_value(n, ms, world), clocks=clocks)
         # correctness of the timed outputs: bound and moments via decompression
         f = aeqc.decompress_batch(model, grid, out, prm)
         st = out.status.cpu().numpy()
@@ -440,7 +451,7 @@ def cpu_baseline(args, cfg, model, budget_s, rank=0):
     def run(k):
         idx = np.linspace(0, n_full - 1, k).astype(np.int64)
         x = synth.histograms(n_full if n_full <= 65536 else max(idx) + 1,
-                             synth.config_seed(1) + 1000 * rank, k_max=cfg["k_max"],
+                             shard_seed(synth, rank), k_max=cfg["k_max"],
                              heavy_frac=cfg["heavy"], idx=idx) if n_full <= 65536 else \
             _sample_histograms(synth, cfg, n_full, idx, rank)
         t0 = time.time()
@@ -461,7 +472,7 @@ def cpu_baseline(args, cfg, model, budget_s, rank=0):
 
 
 def _sample_histograms(synth, cfg, n_full, idx, rank):
-    return synth.histograms(n_full, synth.config_seed(1) + 1000 * rank, k_max=cfg["k_max"],
+    return synth.histograms(n_full, shard_seed(synth, rank), k_max=cfg["k_max"],
                             heavy_frac=cfg["heavy"], idx=idx)
 
 

@@ -330,6 +330,29 @@ int compress_batch(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* grid, const do
                    void* stream);
 size_t compress_batch_workspace_size(const aeqc_model* m, int64_t n);
 
+/* compress_batch from HOST memory to HOST memory, streamed: the batch is cut
+ * into chunks of `chunk` histograms; each chunk's input is copied to the
+ * device, compressed and its outputs copied back, on three streams (the
+ * caller's for compute, two library-owned ones for the copies) with two
+ * device buffers, so the copies of one chunk overlap the compute of the
+ * next.  Same results as compress_batch on the whole batch.
+ *   x_host   [n][P] float64, host (page-locked for the copies to overlap)
+ *   out_host aeqc_compressed whose arrays are HOST arrays of the full batch
+ *            (latent [n][L], scale, codes [n][P], lambda [n][4], iters,
+ *            status, outliers with global indices; features must be NULL);
+ *            outliers.count is written at the end
+ *   chunk    histograms per chunk (> 0)
+ * Single-group models only (AEQC_EUNSUPPORTED otherwise).  The workspace
+ * (compress_batch_host_workspace_size) holds the two device buffers.  On
+ * return the work is enqueued; the caller's stream is ordered after the last
+ * copy (synchronise it before reading out_host). */
+int compress_batch_host(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* grid,
+                        const double* x_host, int64_t n, const aeqc_params* params,
+                        aeqc_compressed* out_host, int64_t chunk, void* workspace,
+                        size_t workspace_bytes, void* stream);
+size_t compress_batch_host_workspace_size(const aeqc_model* m, int64_t chunk,
+                                          int64_t outlier_capacity);
+
 /* Decompression (end of Stage 5): decode the latents, x' from the codes,
  * f = x' exp(-lambda.phi) at every point (raw values at escapes, also
  * corrected), f [n][P] float64. */

@@ -117,6 +117,10 @@ SYMBOLS = {
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                                  C.c_void_p]),
     "compress_batch_workspace_size": (C.c_size_t, [C.c_void_p, C.c_int64]),
+    "compress_batch_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_int64, C.c_void_p, C.c_void_p, C.c_int64,
+                                      C.c_void_p, C.c_size_t, C.c_void_p]),
+    "compress_batch_host_workspace_size": (C.c_size_t, [C.c_void_p, C.c_int64, C.c_int64]),
     "quantize_correct": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
                                    C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
@@ -453,6 +457,55 @@ class Compressed:
             aeqc_outliers(int(outlier_capacity), _ptr(self.count), _ptr(self.index),
                           _ptr(self.value)),
             _ptr(self.features))
+
+
+class CompressedHost(Compressed):
+    """Page-locked HOST buffers of a compressed batch (for compress_batch_host)."""
+
+    def __init__(self, n: int, P: int, L: int, latent_dtype, outlier_capacity: int):
+        import torch
+        self.n = n
+        pin = dict(device="cpu", pin_memory=True)
+        self.latent = torch.empty((n, L), dtype=latent_dtype, **pin)
+        self.scale = torch.empty(n, dtype=torch.float64, **pin)
+        self.codes = torch.empty((n, P), dtype=torch.int16, **pin)
+        self.lam = torch.empty((n, 4), dtype=torch.float64, **pin)
+        self.iters = torch.empty(n, dtype=torch.uint8, **pin)
+        self.status = torch.empty(n, dtype=torch.uint16, **pin)
+        self.count = torch.zeros(1, dtype=torch.int64, **pin)
+        cap = max(int(outlier_capacity), 1)
+        self.index = torch.empty(cap, dtype=torch.int64, **pin)
+        self.value = torch.empty(cap, dtype=torch.float64, **pin)
+        self.features = None
+        self.c = aeqc_compressed(
+            _ptr(self.latent), _ptr(self.scale), _ptr(self.codes), _ptr(self.lam),
+            _ptr(self.iters), _ptr(self.status),
+            aeqc_outliers(int(outlier_capacity), _ptr(self.count), _ptr(self.index),
+                          _ptr(self.value)),
+            None)
+
+
+def compress_batch_host(m: Model, grid: Grid, x_host, params: aeqc_params, chunk: int = 1 << 17,
+                        mlp: Optional[MLP] = None, out: Optional[CompressedHost] = None,
+                        ws=None, outlier_capacity: Optional[int] = None, device=None,
+                        stream=None) -> CompressedHost:
+    """compress_batch from a (page-locked) host array into host buffers, with
+    the copies of one chunk overlapping the compute of the next."""
+    import torch
+    n, P = x_host.shape
+    cap = outlier_capacity if outlier_capacity is not None else max(1024, 4 * n)
+    if out is None:
+        out = CompressedHost(n, P, m.L, m.latent_dtype(), cap)
+    cap = out.c.outliers.capacity
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    need = load().compress_batch_host_workspace_size(m.h, min(chunk, n), cap)
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, device)
+    _check(load().compress_batch_host(m.h, mlp.h if mlp is not None else None, C.byref(grid.c),
+                                      _ptr(x_host), n, C.byref(params), C.byref(out.c), chunk,
+                                      _ptr(ws), ws.numel(), _stream(stream)))
+    out.ws = ws
+    return out
 
 
 def compress_batch_workspace(m: Model, n: int, device):

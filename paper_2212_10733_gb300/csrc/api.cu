@@ -99,19 +99,19 @@ static int run_quantize_correct(const GridK& gk, const ParamsK& pk, int kernel,
                                 const double* x, const float* xhat, long long ld, long long n,
                                 aeqc_mlp* mlp, int latent_dtype, int latent_dim,
                                 aeqc_compressed* out, double* f_out, char* ws, size_t ws_bytes,
-                                cudaStream_t s) {
+                                cudaStream_t s, long long row0 = 0, bool reset_count = true) {
   WsCarver c(ws, ws_bytes);
   int* fb_list = c.take<int>((size_t)n);
   int* fb_count = c.take<int>(1);
   if (!c.ok()) return set_error(AEQC_EINVAL, "quantize_correct: workspace too small");
-  AEQC_CUDA_TRY(cudaMemsetAsync(out->outliers.count, 0, sizeof(int64_t), s));
+  if (reset_count) AEQC_CUDA_TRY(cudaMemsetAsync(out->outliers.count, 0, sizeof(int64_t), s));
   FusedArgs a;
   memset(&a, 0, sizeof(a));
   a.x = x;
   a.xhat = xhat;
   a.ldx = ld;
   a.n = n;
-  a.row0 = 0;
+  a.row0 = row0;
   a.grid = gk;
   a.prm = pk;
   a.codes = out->codes;
@@ -378,6 +378,218 @@ extern "C" int quantize_correct(const aeqc_grid* grid, const double* x, const fl
   return run_quantize_correct(gk, pk, params->kernel, x, xhat, ld, n, mlp, latent_dtype,
                               latent_dim, out, f_out, static_cast<char*>(workspace),
                               workspace_bytes, static_cast<cudaStream_t>(stream));
+}
+
+// ---- compress_batch from host memory, streamed ---------------------------------
+
+namespace aeqc {
+
+// copy streams, created once per device and kept for the process lifetime
+struct CopyStreams {
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+};
+static std::mutex g_cs_mu;
+static CopyStreams g_cs[64];
+
+static int copy_streams(CopyStreams* out) {
+  int dev = 0;
+  AEQC_CUDA_TRY(cudaGetDevice(&dev));
+  AEQC_CHECK_ARG(dev >= 0 && dev < 64, "compress_batch_host: device ordinal %d >= 64", dev);
+  std::lock_guard<std::mutex> lock(g_cs_mu);
+  if (!g_cs[dev].h2d) {
+    AEQC_CUDA_TRY(cudaStreamCreateWithFlags(&g_cs[dev].h2d, cudaStreamNonBlocking));
+    AEQC_CUDA_TRY(cudaStreamCreateWithFlags(&g_cs[dev].d2h, cudaStreamNonBlocking));
+  }
+  *out = g_cs[dev];
+  return AEQC_OK;
+}
+
+// one device buffer of the pipeline
+struct HostChunkBuf {
+  double* x;
+  void* latent;
+  double* scale;
+  int16_t* codes;
+  double* lambda;
+  uint8_t* iters;
+  uint16_t* status;
+  char* ws;
+  size_t ws_bytes;
+};
+
+static size_t host_buf_bytes(const aeqc_model* m, long long chunk) {
+  const size_t esz = m->d.dtype == AEQC_DTYPE_BF16 ? 2 : 4;
+  WsSize w;
+  w.add<double>((size_t)chunk * m->d.P);
+  w.add<char>((size_t)chunk * m->d.L * esz);
+  w.add<double>((size_t)chunk);
+  w.add<int16_t>((size_t)chunk * m->d.P);
+  w.add<double>((size_t)chunk * 4);
+  w.add<uint8_t>((size_t)chunk);
+  w.add<uint16_t>((size_t)chunk);
+  w.add<char>(compress_batch_workspace_size(m, chunk));
+  return w.bytes;
+}
+
+static bool carve_buf(WsCarver& c, const aeqc_model* m, long long chunk, HostChunkBuf& b) {
+  const size_t esz = m->d.dtype == AEQC_DTYPE_BF16 ? 2 : 4;
+  b.x = c.take<double>((size_t)chunk * m->d.P);
+  b.latent = c.take<char>((size_t)chunk * m->d.L * esz);
+  b.scale = c.take<double>((size_t)chunk);
+  b.codes = c.take<int16_t>((size_t)chunk * m->d.P);
+  b.lambda = c.take<double>((size_t)chunk * 4);
+  b.iters = c.take<uint8_t>((size_t)chunk);
+  b.status = c.take<uint16_t>((size_t)chunk);
+  b.ws_bytes = compress_batch_workspace_size(m, chunk);
+  b.ws = c.take<char>(b.ws_bytes);
+  return c.ok();
+}
+
+}  // namespace aeqc
+
+extern "C" size_t compress_batch_host_workspace_size(const aeqc_model* m, int64_t chunk,
+                                                     int64_t outlier_capacity) {
+  if (!m || chunk <= 0) return 0;
+  WsSize w;
+  w.add<long long>(1);                                       // outlier count
+  w.add<long long>((size_t)(outlier_capacity > 0 ? outlier_capacity : 1));  // indices
+  w.add<double>((size_t)(outlier_capacity > 0 ? outlier_capacity : 1));     // values
+  return w.bytes + 2 * host_buf_bytes(m, chunk) + kWsAlign;
+}
+
+extern "C" int compress_batch_host(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* grid,
+                                   const double* x_host, int64_t n, const aeqc_params* params,
+                                   aeqc_compressed* out_host, int64_t chunk, void* workspace,
+                                   size_t workspace_bytes, void* stream) {
+  clear_error();
+  GridK gk;
+  ParamsK pk;
+  int rc = make_grid(grid, &gk);
+  if (rc) return rc;
+  if ((rc = make_params(params, &pk))) return rc;
+  AEQC_CHECK_ARG(m && out_host, "compress_batch_host: null argument");
+  if (m->d.n_groups != 1)
+    return set_error(AEQC_EUNSUPPORTED, "compress_batch_host: single-group models only");
+  AEQC_CHECK_ARG(m->d.P == gk.P, "compress_batch_host: model P=%d but grid has %d cells",
+                 m->d.P, gk.P);
+  AEQC_CHECK_ARG(n >= 0 && chunk > 0, "compress_batch_host: need n >= 0 and chunk > 0");
+  if (n == 0) return AEQC_OK;
+  const aeqc_compressed& o = *out_host;
+  AEQC_CHECK_ARG(x_host && o.latent && o.scale && o.codes && o.lambda && o.iters && o.status &&
+                     o.outliers.count && !o.features,
+                 "compress_batch_host: null output array (or features set)");
+  AEQC_CHECK_ARG(o.outliers.capacity == 0 || (o.outliers.index && o.outliers.value),
+                 "compress_batch_host: outlier arrays missing");
+  if (mlp) AEQC_CHECK_ARG(mlp->nin == m->d.L + 4, "compress_batch_host: MLP expects %d inputs",
+                          mlp->nin);
+  if (chunk > n) chunk = n;
+  const size_t need = compress_batch_host_workspace_size(m, chunk, o.outliers.capacity);
+  AEQC_CHECK_ARG(workspace && workspace_bytes >= need && aligned(workspace, kWsAlign),
+                 "compress_batch_host: 256-byte aligned workspace of %zu bytes needed", need);
+  CopyStreams cs;
+  if ((rc = copy_streams(&cs))) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  WsCarver c(static_cast<char*>(workspace), workspace_bytes);
+  long long* d_count = c.take<long long>(1);
+  const long long cap = o.outliers.capacity;
+  long long* d_index = c.take<long long>((size_t)(cap > 0 ? cap : 1));
+  double* d_value = c.take<double>((size_t)(cap > 0 ? cap : 1));
+  HostChunkBuf buf[2];
+  if (!carve_buf(c, m, chunk, buf[0]) || !carve_buf(c, m, chunk, buf[1]))
+    return set_error(AEQC_EINVAL, "compress_batch_host: workspace too small");
+  const size_t esz = m->d.dtype == AEQC_DTYPE_BF16 ? 2 : 4;
+  const int P = m->d.P, L = m->d.L;
+  // events: h2d done, compute done, d2h done, per buffer
+  cudaEvent_t ev[2][3];
+  for (int b = 0; b < 2; ++b)
+    for (int k = 0; k < 3; ++k)
+      AEQC_CUDA_TRY(cudaEventCreateWithFlags(&ev[b][k], cudaEventDisableTiming));
+  auto cleanup = [&]() {
+    for (int b = 0; b < 2; ++b)
+      for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[b][k]);
+  };
+  // the copy streams start after the work already on the caller's stream
+  cudaEvent_t start;
+  AEQC_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  AEQC_CUDA_TRY(cudaEventRecord(start, s));
+  AEQC_CUDA_TRY(cudaStreamWaitEvent(cs.h2d, start, 0));
+  AEQC_CUDA_TRY(cudaStreamWaitEvent(cs.d2h, start, 0));
+  cudaEventDestroy(start);
+  AEQC_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(long long), s));
+  const long long nchunks = (n + chunk - 1) / chunk;
+  rc = AEQC_OK;
+  for (long long ci = 0; ci < nchunks && rc == AEQC_OK; ++ci) {
+    const int b = (int)(ci & 1);
+    HostChunkBuf& B = buf[b];
+    const long long c0 = ci * chunk, rows = (c0 + chunk <= n) ? chunk : n - c0;
+    // input: after the compute of chunk ci - 2 has read this buffer
+    if (ci >= 2) AEQC_CUDA_TRY(cudaStreamWaitEvent(cs.h2d, ev[b][1], 0));
+    AEQC_CUDA_TRY(cudaMemcpyAsync(B.x, x_host + c0 * P, sizeof(double) * rows * P,
+                                  cudaMemcpyHostToDevice, cs.h2d));
+    AEQC_CUDA_TRY(cudaEventRecord(ev[b][0], cs.h2d));
+    // compute: after the input and after the copy-out of chunk ci - 2
+    AEQC_CUDA_TRY(cudaStreamWaitEvent(s, ev[b][0], 0));
+    if (ci >= 2) AEQC_CUDA_TRY(cudaStreamWaitEvent(s, ev[b][2], 0));
+    aeqc_compressed dc;
+    memset(&dc, 0, sizeof(dc));
+    dc.latent = B.latent;
+    dc.scale = B.scale;
+    dc.codes = B.codes;
+    dc.lambda = B.lambda;
+    dc.iters = B.iters;
+    dc.status = B.status;
+    dc.outliers.capacity = cap;
+    dc.outliers.count = reinterpret_cast<int64_t*>(d_count);
+    dc.outliers.index = reinterpret_cast<int64_t*>(d_index);
+    dc.outliers.value = d_value;
+    float* xhat = reinterpret_cast<float*>(B.ws);
+    char* rest = B.ws + ws_round(sizeof(float) * (size_t)rows * AEQC_XHAT_LD);
+    const size_t rest_bytes = B.ws_bytes - ws_round(sizeof(float) * (size_t)rows * AEQC_XHAT_LD);
+    if ((rc = run_encode(m, B.x, rows, nullptr, dc.latent, dc.scale, rest, rest_bytes, s))) break;
+    if ((rc = run_decode(m, dc.latent, dc.scale, rows, nullptr, xhat, AEQC_XHAT_LD, rest,
+                         rest_bytes, s)))
+      break;
+    if ((rc = run_quantize_correct(gk, pk, params->kernel, B.x, xhat, AEQC_XHAT_LD, rows, mlp,
+                                   m->d.dtype, L, &dc, nullptr, rest, rest_bytes, s, c0,
+                                   false)))
+      break;
+    AEQC_CUDA_TRY(cudaEventRecord(ev[b][1], s));
+    // outputs
+    AEQC_CUDA_TRY(cudaStreamWaitEvent(cs.d2h, ev[b][1], 0));
+    char* lat_h = static_cast<char*>(o.latent) + (size_t)c0 * L * esz;
+    AEQC_CUDA_TRY(cudaMemcpyAsync(lat_h, B.latent, (size_t)rows * L * esz,
+                                  cudaMemcpyDeviceToHost, cs.d2h));
+    AEQC_CUDA_TRY(cudaMemcpyAsync(o.scale + c0, B.scale, sizeof(double) * rows,
+                                  cudaMemcpyDeviceToHost, cs.d2h));
+    AEQC_CUDA_TRY(cudaMemcpyAsync(o.codes + c0 * P, B.codes, sizeof(int16_t) * rows * P,
+                                  cudaMemcpyDeviceToHost, cs.d2h));
+    AEQC_CUDA_TRY(cudaMemcpyAsync(o.lambda + c0 * 4, B.lambda, sizeof(double) * rows * 4,
+                                  cudaMemcpyDeviceToHost, cs.d2h));
+    AEQC_CUDA_TRY(cudaMemcpyAsync(o.iters + c0, B.iters, rows, cudaMemcpyDeviceToHost, cs.d2h));
+    AEQC_CUDA_TRY(cudaMemcpyAsync(o.status + c0, B.status, sizeof(uint16_t) * rows,
+                                  cudaMemcpyDeviceToHost, cs.d2h));
+    AEQC_CUDA_TRY(cudaEventRecord(ev[b][2], cs.d2h));
+  }
+  if (rc == AEQC_OK) {
+    // the outlier list after the last compute, then the caller's stream waits
+    // for every copy
+    cudaError_t e = cudaStreamWaitEvent(cs.d2h, ev[(nchunks - 1) & 1][1], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(o.outliers.count, d_count, sizeof(long long), cudaMemcpyDeviceToHost,
+                          cs.d2h);
+    if (e == cudaSuccess && cap > 0)
+      e = cudaMemcpyAsync(o.outliers.index, d_index, sizeof(long long) * cap,
+                          cudaMemcpyDeviceToHost, cs.d2h);
+    if (e == cudaSuccess && cap > 0)
+      e = cudaMemcpyAsync(o.outliers.value, d_value, sizeof(double) * cap,
+                          cudaMemcpyDeviceToHost, cs.d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0][2], cs.d2h);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[0][2], 0);
+    if (e != cudaSuccess)
+      rc = set_error(AEQC_ECUDA, "compress_batch_host: %s", cudaGetErrorString(e));
+  }
+  cleanup();
+  return rc;
 }
 
 extern "C" int decompress_batch(aeqc_model* m, const aeqc_grid* grid,

@@ -379,12 +379,16 @@ struct DecArgs {
   long long b4_gs;
   float* xhat;
   long long ld;
+  int sw;  // staging width (32 or 16 columns)
   int* err;
 };
 
 struct DecSmem {
-  uint32_t h, stages, d1a, d1b, bars, total;
-  __host__ __device__ DecSmem(int H, int ns) {
+  uint32_t h, stages, d1a, d1b, stg, bars, total;
+  // sw: columns of the per-warp staging block (32 rows x sw, pitch sw + 1)
+  // through which the epilogue turns row-per-thread values into row-contiguous
+  // coalesced stores
+  __host__ __device__ DecSmem(int H, int ns, int sw) {
     h = 0;  // BF16 h tile: (H / 64) blocks of 128 rows x 128 B
     uint32_t o = (uint32_t)BM * H * 2;
     stages = o;  // B stages: 256 rows x 128 B each; D1 operands alias them
@@ -393,6 +397,8 @@ struct DecSmem {
     d1b = stages + A_STAGE;          // W3 tile [H rows][64]: H * 128 B
     const uint32_t d1 = A_STAGE + (uint32_t)H * 128;
     o += st > d1 ? st : d1;
+    stg = o;
+    o += NCONV * 32 * (sw + 1) * 4;
     bars = o;
     o += 8 * (2 * ns + 8) + 16;
     total = o;
@@ -404,7 +410,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                            ~uintptr_t(1023));
-  const DecSmem L(a.H, a.ns);
+  const DecSmem L(a.H, a.ns, a.sw);
   const int ns = a.ns;
   uint64_t* full_b = reinterpret_cast<uint64_t*>(sm + L.bars);
   uint64_t* empty = full_b + ns;
@@ -581,9 +587,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_fence_before();
     mbar_arrive(h_full);
     // ---- D2 epilogue per 256-column tile: xhat = s (acc + b4) ----
+    // each thread holds one row; the values go through a per-warp staging
+    // block so that every store instruction writes whole rows segments
     const float* b4 = a.b4 + ti.g * a.b4_gs;
     const float rs = r < rows ? (float)a.scale[ti.m0 + r] : 0.f;
-    float* xr = a.xhat + (ti.m0 + r) * a.ld;
+    const int sw = a.sw;
+    float* stg = reinterpret_cast<float*>(sm + L.stg) + warp * 32 * (sw + 1);
+    const int rpi = 32 / sw;                    // rows per store instruction
+    const int sub_r = lane / sw, sub_c = lane % sw;
     for (int j = 0; j < ntiles; ++j) {
       const int buf = j & 1;
       if (ok && (*abort_flag || !mbar_wait(&acc_full[buf], (j >> 1) & 1))) {
@@ -598,20 +609,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + col), v);
           const int p0 = j * 256 + col;
-          if (r < rows) {
-            if (p0 + 32 <= a.P) {
 #pragma unroll
-              for (int u = 0; u < 8; ++u) {
-                float4 o;
-                o.x = rs * (v[4 * u + 0] + __ldg(b4 + p0 + 4 * u + 0));
-                o.y = rs * (v[4 * u + 1] + __ldg(b4 + p0 + 4 * u + 1));
-                o.z = rs * (v[4 * u + 2] + __ldg(b4 + p0 + 4 * u + 2));
-                o.w = rs * (v[4 * u + 3] + __ldg(b4 + p0 + 4 * u + 3));
-                *reinterpret_cast<float4*>(xr + p0 + 4 * u) = o;
+          for (int h0 = 0; h0 < 32; h0 += 16) {
+            if (sw == 16 || h0 == 0) {
+              __syncwarp();
+              const int nc = sw == 16 ? 16 : 32;
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const int pc = p0 + h0 + i;
+                stg[lane * (sw + 1) + i] = rs * (v[h0 + i] + (pc < a.P ? __ldg(b4 + pc) : 0.f));
               }
-            } else {
-              for (int i = 0; i < 32 && p0 + i < a.P; ++i)
-                xr[p0 + i] = rs * (v[i] + __ldg(b4 + p0 + i));
+              if (nc == 32) {
+#pragma unroll
+                for (int i = 16; i < 32; ++i) {
+                  const int pc = p0 + i;
+                  stg[lane * (sw + 1) + i] = rs * (v[i] + (pc < a.P ? __ldg(b4 + pc) : 0.f));
+                }
+              }
+              __syncwarp();
+              // rows q*32 + rr .. of this warp, columns p0 + h0 + sub_c
+              const int pcol = p0 + (sw == 16 ? h0 : 0) + sub_c;
+              for (int rr = sub_r; rr < 32; rr += rpi) {
+                const int row = q * 32 + rr;
+                if (row < rows && pcol < a.P)
+                  a.xhat[(ti.m0 + row) * a.ld + pcol] = stg[rr * (sw + 1) + sub_c];
+              }
             }
           }
         }
@@ -742,10 +764,13 @@ int run_decode_tc(aeqc_model* m, const void* latent, const double* scale, long l
   a.xhat = xhat;
   a.ld = ld;
   a.err = err;
-  int ns = 4;
-  while (ns > 2 && DecSmem(d.H, ns).total + 1024 > 227 * 1024) --ns;
+  // deepest pipeline with the full staging width that fits, else half width
+  int ns = 4, sw = 32;
+  while (ns > 2 && DecSmem(d.H, ns, sw).total + 1024 > 227 * 1024) --ns;
+  if (DecSmem(d.H, ns, sw).total + 1024 > 227 * 1024) sw = 16;
   a.ns = ns;
-  const size_t smem = DecSmem(d.H, ns).total + 1024;
+  a.sw = sw;
+  const size_t smem = DecSmem(d.H, ns, sw).total + 1024;
   if (smem > 227 * 1024) return set_error(AEQC_EUNSUPPORTED, "decoder tile does not fit (H=%d)", d.H);
   AEQC_CUDA_TRY(cudaFuncSetAttribute(dec_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));

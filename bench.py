@@ -175,8 +175,8 @@ def build_workload(cfg, n, rank, device, aq, synth, train_steps=None):
     seed = shard_seed(synth, rank)
     x = synth.histograms_torch(n, seed, device, k_max=cfg["k_max"], heavy_frac=cfg["heavy"])
     P, H, L = synth.P, cfg["H"], cfg["L"]
-    dtype = aq.DTYPE_BF16 if cfg["dtype"] == "bf16" else aq.DTYPE_F32
-    model = aq.Model(P, H, L, tied=True, act=aq.ACT_IDENTITY, dtype=dtype)
+    # FP32 master weights; each form builds its model from them
+    model = aq.Model(P, H, L, tied=True, act=aq.ACT_IDENTITY, dtype=aq.DTYPE_F32)
     model.set_group(0, synth.ae_init(P, H, L, seed))
     model.fit_normalizer(0, x[: min(n, 1 << 16)])
     B = cfg["batch"]
@@ -299,9 +299,7 @@ def run_ours(args, rank, world, local):
         ms = max_over_ranks(ms, world)
         r = dict(ms=ms, value=job_value(n, ms, world), clocks=clocks)
         # correctness of the timed outputs: bound and moments via decompression
-        f = aeqc.decompress_batch(model, grid, out, prm)
         st = out.status.cpu().numpy()
-        e = cfg["tau"] * x.amax(dim=1, keepdim=True)
         r["stats"] = dict(
             converged_round1=float(np.mean((st & aeqc.ST_CONVERGED) != 0)),
             verbatim=float(np.mean((st & aeqc.ST_VERBATIM) != 0)),
@@ -309,9 +307,7 @@ def run_ours(args, rank, world, local):
             ae_exact=float(np.mean((st & aeqc.ST_AE_EXACT) != 0)),
             mean_iters=float(out.iters.float().mean().item()),
             outliers=int(out.count.item()),
-            max_err_over_bound=float(((f - x).abs() / e).max().item()),
-            max_qoi_rel_err=qoi_rel_err(aeqc, grid, f, x))
-        del f
+            **check_outputs(aeqc, grid, model, out, x, prm, cfg["tau"]))
         # per-stage times on the same stream and launch configuration
         hbuf = torch.empty((n, aeqc.XHAT_LD), dtype=torch.float32, device=device)
         hbuf.copy_(aeqc.ae_decode(model, out.latent, out.scale))
@@ -417,6 +413,41 @@ def run_ours(args, rank, world, local):
             "speedup": round(head["value"] / r["value"], 2), "stage_ms": r["stage_ms"],
             "stats": r["stats"], "clocks": r["clocks"]}
     return res, trained, cfg
+
+
+def check_outputs(aeqc, grid, model, out, x, prm, tau, chunk=1 << 20):
+    """Decompress the batch (in row chunks when no point escaped: escaped
+    values are addressed by global index) and measure max |f - x| / e and the
+    relative QoI error over all histograms."""
+    n = x.shape[0]
+    if int(out.count.item()) > 0:
+        chunk = n
+    e_max, q_max = 0.0, 0.0
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        view = SubView(aeqc, out, c0, c1)
+        f = aeqc.decompress_batch(model, grid, view, prm)
+        xs = x[c0:c1]
+        e = tau * xs.amax(dim=1, keepdim=True)
+        e_max = max(e_max, float(((f - xs).abs() / e).max().item()))
+        q_max = max(q_max, qoi_rel_err(aeqc, grid, f, xs))
+        del f
+    return {"max_err_over_bound": e_max, "max_qoi_rel_err": q_max}
+
+
+class SubView:
+    """Rows [c0, c1) of a compressed batch, as decompress_batch takes it."""
+
+    def __init__(self, aeqc, out, c0, c1):
+        def off(t):
+            return t.data_ptr() + c0 * t.stride(0) * t.element_size()
+        self.n = c1 - c0
+        self.codes = out.codes[c0:c1]
+        self.c = aeqc.aeqc_compressed(
+            off(out.latent), off(out.scale), off(out.codes), off(out.lam), off(out.iters),
+            off(out.status),
+            aeqc.aeqc_outliers(out.c.outliers.capacity, out.count.data_ptr(),
+                               out.index.data_ptr(), out.value.data_ptr()), None)
 
 
 def qoi_rel_err(aeqc, grid, f, x):

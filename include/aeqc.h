@@ -142,6 +142,22 @@ typedef struct aeqc_model aeqc_model;
 int aeqc_model_create(const aeqc_model_desc* desc, aeqc_model** out);
 int aeqc_model_destroy(aeqc_model* m);
 
+/* Launch choices of a model's kernels (no effect on results, only on speed).
+ * 0 in a field selects the built-in default.
+ *   enc_stages, dec_stages  pipeline depth of the BF16 tensor-core encoder /
+ *                           decoder (2..6 / 2..4; reduced to what fits in
+ *                           shared memory)
+ *   qc_ctas_per_sm          CTAs of the correction kernel per SM (1..4) in
+ *                           compress_batch and compress_batch_host */
+typedef struct aeqc_tuning {
+  int32_t enc_stages;
+  int32_t dec_stages;
+  int32_t qc_ctas_per_sm;
+  int32_t reserved;
+} aeqc_tuning;
+int aeqc_model_set_tuning(aeqc_model* m, const aeqc_tuning* t);
+int aeqc_model_get_tuning(const aeqc_model* m, aeqc_tuning* t);
+
 /* Sets (synchronously) the parameters of one group from HOST float64 arrays:
  * W1 [P][H], b1 [H], W2 [H][L], b2 [L], b3 [H], b4 [P], mu [P], sigma [P]
  * (per-pixel Z-score of x / max(x), Sec. IV-C), and for untied models
@@ -329,6 +345,18 @@ int compress_batch(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* grid, const do
                    aeqc_compressed* out, void* workspace, size_t workspace_bytes,
                    void* stream);
 size_t compress_batch_workspace_size(const aeqc_model* m, int64_t n);
+
+/* Autotuner of the launch choices (aeqc_tuning) for this model on this batch:
+ * times every candidate of each stage (encoder pipeline depths, decoder
+ * pipeline depths, correction-kernel CTAs per SM) with CUDA events on
+ * `stream`, keeps the fastest in the model and returns it in *best.
+ * Arguments as compress_batch (the outputs are written, as by compress_batch
+ * with the chosen tuning).  Synchronises the stream; not for use during
+ * stream capture.  The paper has no counterpart. */
+int aeqc_autotune(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* grid, const double* x,
+                  int64_t n, const int64_t* group_offsets, const aeqc_params* params,
+                  aeqc_compressed* out, void* workspace, size_t workspace_bytes, void* stream,
+                  aeqc_tuning* best);
 
 /* compress_batch from HOST memory to HOST memory, streamed: the batch is cut
  * into chunks of `chunk` histograms; each chunk's input is copied to the

@@ -68,6 +68,11 @@ class aeqc_model_desc(C.Structure):
                                           "reserved")]
 
 
+class aeqc_tuning(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("enc_stages", "dec_stages", "qc_ctas_per_sm",
+                                          "reserved")]
+
+
 class aeqc_outliers(C.Structure):
     _fields_ = [("capacity", C.c_int64), ("count", C.c_void_p), ("index", C.c_void_p),
                 ("value", C.c_void_p)]
@@ -86,6 +91,11 @@ SYMBOLS = {
     "aeqc_version": (C.c_char_p, []),
     "aeqc_model_create": (C.c_int, [C.c_void_p, C.c_void_p]),
     "aeqc_model_destroy": (C.c_int, [C.c_void_p]),
+    "aeqc_model_set_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "aeqc_model_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "aeqc_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                C.c_void_p, C.c_void_p]),
     "aeqc_model_set_group": (C.c_int, [C.c_void_p, C.c_int32] + [C.c_void_p] * 10),
     "aeqc_model_get_group": (C.c_int, [C.c_void_p, C.c_int32] + [C.c_void_p] * 10),
     "aeqc_fit_normalizer": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64,
@@ -343,6 +353,16 @@ class Model:
                                    _ptr(ws), ws.numel(), _stream(stream)))
         return loss, g
 
+    def set_tuning(self, enc_stages: int = 0, dec_stages: int = 0, qc_ctas_per_sm: int = 0):
+        t = aeqc_tuning(enc_stages, dec_stages, qc_ctas_per_sm, 0)
+        _check(load().aeqc_model_set_tuning(self.h, C.byref(t)))
+
+    def get_tuning(self) -> dict:
+        t = aeqc_tuning()
+        _check(load().aeqc_model_get_tuning(self.h, C.byref(t)))
+        return dict(enc_stages=t.enc_stages, dec_stages=t.dec_stages,
+                    qc_ctas_per_sm=t.qc_ctas_per_sm)
+
     def latent_dtype(self):
         import torch
         return torch.bfloat16 if self.desc.dtype == DTYPE_BF16 else torch.float32
@@ -506,6 +526,26 @@ def compress_batch_host(m: Model, grid: Grid, x_host, params: aeqc_params, chunk
                                       _ptr(ws), ws.numel(), _stream(stream)))
     out.ws = ws
     return out
+
+
+def autotune(m: Model, grid: Grid, x, params: aeqc_params, mlp: Optional[MLP] = None,
+             group_offsets=None, out: Optional[Compressed] = None, ws=None,
+             outlier_capacity: Optional[int] = None, stream=None) -> dict:
+    """Times the launch choices on this batch, keeps the fastest in the model
+    and returns them (the outputs in `out` are those of compress_batch)."""
+    n = x.shape[0]
+    if out is None:
+        cap = outlier_capacity if outlier_capacity is not None else max(1024, n * 4)
+        out = Compressed(n, m.P, m.L, m.latent_dtype(), x.device, cap)
+    if ws is None:
+        ws = compress_batch_workspace(m, n, x.device)
+    t = aeqc_tuning()
+    _check(load().aeqc_autotune(m.h, mlp.h if mlp is not None else None, C.byref(grid.c),
+                                _ptr(x), n, _ptr(group_offsets), C.byref(params),
+                                C.byref(out.c), _ptr(ws), ws.numel(), _stream(stream),
+                                C.byref(t)))
+    return dict(enc_stages=t.enc_stages, dec_stages=t.dec_stages,
+                qc_ctas_per_sm=t.qc_ctas_per_sm)
 
 
 def compress_batch_workspace(m: Model, n: int, device):

@@ -723,13 +723,18 @@ int run_encode_tc(aeqc_model* m, const double* x, long long n, const long long* 
   a.scale = scale;
   a.err = err;
   // stages: as many as fit next to the W2 tile
-  int ns = 6;
+  // stages: the tuned depth (else 6), reduced to what fits next to the W2 tile
+  int ns = m->tuning.enc_stages >= 2 && m->tuning.enc_stages <= 6 ? m->tuning.enc_stages : 6;
   while (ns > 2 && EncSmem(d.H, d.L, ns).total + 1024 > 227 * 1024) --ns;
   a.ns = ns;
   const size_t smem = EncSmem(d.H, d.L, ns).total + 1024;
   if (smem > 227 * 1024) return set_error(AEQC_EUNSUPPORTED, "encoder tile does not fit (H=%d)", d.H);
-  AEQC_CUDA_TRY(cudaFuncSetAttribute(enc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+  static size_t enc_attr = 0;  // the attribute is raised once (capture-safe afterwards)
+  if (smem > enc_attr) {
+    AEQC_CUDA_TRY(cudaFuncSetAttribute(enc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024));
+    enc_attr = 227 * 1024;
+  }
   const long long tiles = G > 1 ? (n + BM - 1) / BM + G : (n + BM - 1) / BM;
   enc_tc_kernel<<<(unsigned)tiles, NTHREADS, smem, s>>>(mW1, mW2, a);
   return check_launch("enc_tc_kernel");
@@ -765,15 +770,20 @@ int run_decode_tc(aeqc_model* m, const void* latent, const double* scale, long l
   a.ld = ld;
   a.err = err;
   // deepest pipeline with the full staging width that fits, else half width
-  int ns = 4, sw = 32;
+  int ns = m->tuning.dec_stages >= 2 && m->tuning.dec_stages <= 4 ? m->tuning.dec_stages : 4;
+  int sw = 32;
   while (ns > 2 && DecSmem(d.H, ns, sw).total + 1024 > 227 * 1024) --ns;
   if (DecSmem(d.H, ns, sw).total + 1024 > 227 * 1024) sw = 16;
   a.ns = ns;
   a.sw = sw;
   const size_t smem = DecSmem(d.H, ns, sw).total + 1024;
   if (smem > 227 * 1024) return set_error(AEQC_EUNSUPPORTED, "decoder tile does not fit (H=%d)", d.H);
-  AEQC_CUDA_TRY(cudaFuncSetAttribute(dec_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+  static size_t dec_attr = 0;
+  if (smem > dec_attr) {
+    AEQC_CUDA_TRY(cudaFuncSetAttribute(dec_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024));
+    dec_attr = 227 * 1024;
+  }
   const long long tiles = G > 1 ? (n + BM - 1) / BM + G : (n + BM - 1) / BM;
   dec_tc_kernel<<<(unsigned)tiles, NTHREADS, smem, s>>>(mW4, a);
   return check_launch("dec_tc_kernel");

@@ -99,7 +99,8 @@ static int run_quantize_correct(const GridK& gk, const ParamsK& pk, int kernel,
                                 const double* x, const float* xhat, long long ld, long long n,
                                 aeqc_mlp* mlp, int latent_dtype, int latent_dim,
                                 aeqc_compressed* out, double* f_out, char* ws, size_t ws_bytes,
-                                cudaStream_t s, long long row0 = 0, bool reset_count = true) {
+                                cudaStream_t s, long long row0 = 0, bool reset_count = true,
+                                int ctas_per_sm = 0) {
   WsCarver c(ws, ws_bytes);
   int* fb_list = c.take<int>((size_t)n);
   int* fb_count = c.take<int>(1);
@@ -131,7 +132,8 @@ static int run_quantize_correct(const GridK& gk, const ParamsK& pk, int kernel,
   if (rc) return rc;
   a.fb_list = fb_list;
   a.fb_count = fb_count;
-  return kernel == AEQC_KERNEL_FAST ? launch_fused_fast(a, s) : launch_fused_fp64(a, s);
+  return kernel == AEQC_KERNEL_FAST ? launch_fused_fast(a, s, ctas_per_sm)
+                                    : launch_fused_fp64(a, s);
 }
 
 }  // namespace aeqc
@@ -341,7 +343,135 @@ extern "C" int compress_batch(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* gri
                        rest_bytes, s)))
     return rc;
   return run_quantize_correct(gk, pk, params->kernel, x, xhat, AEQC_XHAT_LD, n, mlp,
-                              m->d.dtype, m->d.L, out, nullptr, rest, rest_bytes, s);
+                              m->d.dtype, m->d.L, out, nullptr, rest, rest_bytes, s, 0, true,
+                              m->tuning.qc_ctas_per_sm);
+}
+
+// ---- launch tuning --------------------------------------------------------------
+
+extern "C" int aeqc_model_set_tuning(aeqc_model* m, const aeqc_tuning* t) {
+  clear_error();
+  AEQC_CHECK_ARG(m && t, "aeqc_model_set_tuning: null argument");
+  AEQC_CHECK_ARG(t->enc_stages == 0 || (t->enc_stages >= 2 && t->enc_stages <= 6),
+                 "aeqc_model_set_tuning: enc_stages must be 0 or in [2, 6]");
+  AEQC_CHECK_ARG(t->dec_stages == 0 || (t->dec_stages >= 2 && t->dec_stages <= 4),
+                 "aeqc_model_set_tuning: dec_stages must be 0 or in [2, 4]");
+  AEQC_CHECK_ARG(t->qc_ctas_per_sm >= 0 && t->qc_ctas_per_sm <= 4,
+                 "aeqc_model_set_tuning: qc_ctas_per_sm must be in [0, 4]");
+  m->tuning = *t;
+  m->tuning.reserved = 0;
+  return AEQC_OK;
+}
+
+extern "C" int aeqc_model_get_tuning(const aeqc_model* m, aeqc_tuning* t) {
+  clear_error();
+  AEQC_CHECK_ARG(m && t, "aeqc_model_get_tuning: null argument");
+  *t = m->tuning;
+  return AEQC_OK;
+}
+
+namespace aeqc {
+
+// mean time of `reps` calls of f after one untimed call, CUDA events on s
+template <typename F>
+static int time_calls(cudaStream_t s, int reps, F f, float* ms) {
+  int rc = f();
+  if (rc) return rc;
+  cudaEvent_t e0, e1;
+  AEQC_CUDA_TRY(cudaEventCreate(&e0));
+  AEQC_CUDA_TRY(cudaEventCreate(&e1));
+  AEQC_CUDA_TRY(cudaEventRecord(e0, s));
+  for (int r = 0; r < reps && !rc; ++r) rc = f();
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (e != cudaSuccess) return set_error(AEQC_ECUDA, "autotune timing: %s", cudaGetErrorString(e));
+  *ms = t / reps;
+  return AEQC_OK;
+}
+
+}  // namespace aeqc
+
+extern "C" int aeqc_autotune(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* grid,
+                             const double* x, int64_t n, const int64_t* group_offsets,
+                             const aeqc_params* params, aeqc_compressed* out, void* workspace,
+                             size_t workspace_bytes, void* stream, aeqc_tuning* best) {
+  // one ordinary call validates the arguments and leaves the decoded rows in
+  // the workspace
+  int rc = compress_batch(m, mlp, grid, x, n, group_offsets, params, out, workspace,
+                          workspace_bytes, stream);
+  if (rc) return rc;
+  AEQC_CHECK_ARG(best, "aeqc_autotune: null best");
+  if (n == 0) {
+    *best = m->tuning;
+    return AEQC_OK;
+  }
+  GridK gk;
+  ParamsK pk;
+  make_grid(grid, &gk);
+  make_params(params, &pk);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  float* xhat = reinterpret_cast<float*>(ws);
+  char* rest = ws + xhat_bytes(m, n);
+  const size_t rest_bytes = workspace_bytes - xhat_bytes(m, n);
+  const long long* goff = reinterpret_cast<const long long*>(group_offsets);
+  aeqc_tuning t = m->tuning;
+  const int reps = 2;
+  if (m->d.dtype == AEQC_DTYPE_BF16) {
+    float bt = 1e30f;
+    int bv = t.enc_stages;
+    for (int v = 2; v <= 6; ++v) {
+      m->tuning.enc_stages = v;
+      float ms = 0.f;
+      if ((rc = time_calls(s, reps, [&]() {
+             return run_encode(m, x, n, goff, out->latent, out->scale, rest, rest_bytes, s);
+           }, &ms)))
+        break;
+      if (ms < bt) bt = ms, bv = v;
+    }
+    m->tuning.enc_stages = bv;
+    t.enc_stages = bv;
+    bt = 1e30f;
+    bv = t.dec_stages;
+    for (int v = 2; v <= 4 && !rc; ++v) {
+      m->tuning.dec_stages = v;
+      float ms = 0.f;
+      if ((rc = time_calls(s, reps, [&]() {
+             return run_decode(m, out->latent, out->scale, n, goff, xhat, AEQC_XHAT_LD, rest,
+                               rest_bytes, s);
+           }, &ms)))
+        break;
+      if (ms < bt) bt = ms, bv = v;
+    }
+    m->tuning.dec_stages = bv;
+    t.dec_stages = bv;
+  }
+  if (!rc && params->kernel == AEQC_KERNEL_FAST) {
+    float bt = 1e30f;
+    int bv = t.qc_ctas_per_sm;
+    for (int v = 1; v <= 4; ++v) {
+      float ms = 0.f;
+      if ((rc = time_calls(s, reps, [&]() {
+             return run_quantize_correct(gk, pk, params->kernel, x, xhat, AEQC_XHAT_LD, n, mlp,
+                                         m->d.dtype, m->d.L, out, nullptr, rest, rest_bytes, s,
+                                         0, true, v);
+           }, &ms)))
+        break;
+      if (ms < bt) bt = ms, bv = v;
+    }
+    t.qc_ctas_per_sm = bv;
+  }
+  m->tuning = t;
+  if (rc) return rc;
+  *best = t;
+  // the outputs as compress_batch writes them with the chosen tuning
+  return compress_batch(m, mlp, grid, x, n, group_offsets, params, out, workspace,
+                        workspace_bytes, stream);
 }
 
 extern "C" int quantize_correct(const aeqc_grid* grid, const double* x, const float* xhat,
@@ -551,7 +681,7 @@ extern "C" int compress_batch_host(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid
       break;
     if ((rc = run_quantize_correct(gk, pk, params->kernel, B.x, xhat, AEQC_XHAT_LD, rows, mlp,
                                    m->d.dtype, L, &dc, nullptr, rest, rest_bytes, s, c0,
-                                   false)))
+                                   false, m->tuning.qc_ctas_per_sm)))
       break;
     AEQC_CUDA_TRY(cudaEventRecord(ev[b][1], s));
     // outputs

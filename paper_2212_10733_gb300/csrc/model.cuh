@@ -27,6 +27,7 @@ struct aeqc_model {
   long long bE1B, bE2B, bD1B, bD2B, n_bf16;
   int Kp1;  // P padded to a multiple of 64
   int* dev_err;  // device word: nonzero after a tensor-core kernel gave up a wait
+  aeqc_tuning tuning;  // launch choices (zero: defaults)
   bool dirty;
 };
 

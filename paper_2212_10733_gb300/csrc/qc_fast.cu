@@ -958,7 +958,7 @@ int make_fast_grid(const GridK& g, FastGridK* out) {
   return AEQC_OK;
 }
 
-int launch_fused_fast(const FusedArgs& a_in, cudaStream_t s) {
+int launch_fused_fast(const FusedArgs& a_in, cudaStream_t s, int ctas_per_sm) {
   if (a_in.n <= 0) return AEQC_OK;
   FusedArgs a = a_in;
   if (!a.fg.ok || a.prm.loss != 0 || a.grid.has_vol) return launch_fused_fp64(a, s);
@@ -974,7 +974,8 @@ int launch_fused_fast(const FusedArgs& a_in, cudaStream_t s) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   long long blocks = (a.n + FW - 1) / FW;
-  const long long cap = (long long)sms * 4;  // 4 CTAs of 4 warps fit per SM
+  // up to 4 CTAs of 4 warps fit per SM (registers); fewer when tuned so
+  const long long cap = (long long)sms * (ctas_per_sm >= 1 && ctas_per_sm <= 4 ? ctas_per_sm : 4);
   if (blocks > cap) blocks = cap;
   fused_fast_kernel<<<(unsigned)blocks, FW * 32, smem, s>>>(a);
   int rc = check_launch("fused_fast_kernel");

@@ -37,6 +37,12 @@ CONFIGS = {
             epochs=2, steps_train=None, batch=128, dtype="f32"),
     2: dict(name="precision-4M", n=4_194_304, H=512, L=32, tau=1e-4, k_max=4, heavy=0.1,
             epochs=1, steps_train=None, batch=128, dtype="bf16"),
+    # 256 subdomains of lognormal size (median 8192, clipped to [1024, 65536]),
+    # each with its own autoencoder
+    3: dict(name="batching-256-subdomains", n=None, G=256, H=256, L=32, tau=1e-4, k_max=3,
+            heavy=0.0, epochs=1, steps_train=None, batch=128, dtype="bf16"),
+    4: dict(name="warm-start-256-subdomains", n=None, G=256, H=256, L=32, tau=1e-4, k_max=3,
+            heavy=0.0, epochs=1, steps_train=None, batch=128, dtype="bf16", warm=True),
 }
 METRIC = "compress+correct histograms/s (input GB/s) at QoI err<=1e-10, vs plain form"
 HIST_BYTES = 1521 * 8
@@ -83,6 +89,17 @@ def dist_setup(args):
             torch.cuda.set_device(local)
         dist.init_process_group(backend)
     return rank, world, local
+
+
+def workload_size(cfg, args, synth, rank=0) -> int:
+    """Histograms per rank: --n, the config's count, or the sum of its
+    subdomain sizes (scaled to about --n when given)."""
+    if cfg.get("G"):
+        sizes = synth.group_sizes(cfg["G"], shard_seed(synth, rank))
+        if args.n:
+            sizes = np.maximum(1, np.rint(sizes * args.n / sizes.sum())).astype(np.int64)
+        return int(sizes.sum())
+    return int(args.n or cfg["n"])
 
 
 def shard_seed(synth, rank: int) -> int:
@@ -330,6 +347,9 @@ def run_ours(args, rank, world, local):
 
     head = results[args.form]
     model, prm, out, ws = head.pop("ctx")
+    precision = None
+    if cfg["dtype"] == "bf16" and FORMS[args.form]["dtype"] == "bf16":
+        precision = precision_report(aeqc, trained, model, x, grid, out, prm)
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
@@ -405,6 +425,8 @@ def run_ours(args, rank, world, local):
         "roofline": roofline, "gemm": gemm, "e2e": e2e, "training": tr,
         "stats": head["stats"],
     }
+    if precision:
+        res["precision_vs_fp64_oracle"] = precision
     for form, r in results.items():
         if form == args.form:
             continue
@@ -415,18 +437,280 @@ def run_ours(args, rank, world, local):
     return res, trained, cfg
 
 
-def check_outputs(aeqc, grid, model, out, x, prm, tau, chunk=1 << 20):
-    """Decompress the batch (in row chunks when no point escaped: escaped
-    values are addressed by global index) and measure max |f - x| / e and the
-    relative QoI error over all histograms."""
+# --------------------------------------------------------------------------
+# grouped workloads: subdomains with their own autoencoders
+# --------------------------------------------------------------------------
+
+def grouped_workload(cfg, args, rank, device, aq, synth):
+    """Subdomain sizes, histograms, and one FP32 master model with a group of
+    weights per subdomain, each trained on its own subdomain's histograms."""
+    import torch
+    seed = shard_seed(synth, rank)
+    sizes = synth.group_sizes(cfg["G"], seed)
+    if args.n:  # scale the subdomains down to about --n histograms in total
+        sizes = np.maximum(1, np.rint(sizes * args.n / sizes.sum())).astype(np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    x = synth.histograms_torch(n, seed, device, k_max=cfg["k_max"], heavy_frac=cfg["heavy"])
+    P, H, L, G, B = synth.P, cfg["H"], cfg["L"], cfg["G"], cfg["batch"]
+    model = aq.Model(P, H, L, tied=True, act=aq.ACT_IDENTITY, dtype=aq.DTYPE_F32, n_groups=G)
+    t0 = time.time()
+    ws = None
+    loss = torch.zeros(1, device=device)
+    steps_total = 0
+    xb = torch.empty((B, P), dtype=torch.float64, device=device)
+    for g in range(G):
+        xg = x[off[g]:off[g + 1]]
+        model.set_group(g, synth.ae_init(P, H, L, seed + 7 * g))
+        model.fit_normalizer(g, xg[:65536])
+        ng = xg.shape[0]
+        steps = max(1, cfg["epochs"] * ng // B)
+        if args.train_steps is not None:
+            steps = args.train_steps
+        order = torch.randperm(ng, generator=torch.Generator().manual_seed(seed + g)).to(device)
+        for t in range(steps):
+            i0 = (t * B) % max(ng - B + 1, 1)
+            if ng >= B:
+                torch.index_select(xg, 0, order[i0:i0 + B], out=xb)
+                ws = model.train_step(xb, lr=1e-3, group=g, loss_out=loss, ws=ws)
+            else:
+                ws = model.train_step(xg, lr=1e-3, group=g, loss_out=loss, ws=ws)
+        steps_total += steps
+    torch.cuda.synchronize()
+    tr = dict(train_steps=steps_total, train_s=round(time.time() - t0, 2),
+              last_loss=float(loss.item()))
+    return x, sizes, off, model, tr
+
+
+def copy_model(aq, src, cfg, dtype):
+    from paper_2212_10733_gb300 import synth
+    m = aq.Model(synth.P, cfg["H"], cfg["L"], tied=True, act=aq.ACT_IDENTITY, dtype=dtype,
+                 n_groups=cfg["G"])
+    for g in range(cfg["G"]):
+        m.set_group(g, src.get_group(g))
+    return m
+
+
+def group_view(aq, out, r0, r1):
+    """aeqc_compressed over rows [r0, r1) of a device batch (shared outlier list)."""
+    def off(t):
+        return t.data_ptr() + r0 * t.stride(0) * t.element_size()
+    return aq.aeqc_compressed(off(out.latent), off(out.scale), off(out.codes), off(out.lam),
+                              off(out.iters), off(out.status),
+                              aq.aeqc_outliers(out.c.outliers.capacity, out.count.data_ptr(),
+                                               out.index.data_ptr(), out.value.data_ptr()),
+                              None)
+
+
+def precision_report(aeqc, trained, model, x, grid, out, prm, k=256):
+    """Error of the BF16 tensor-core autoencoder against the FP64 oracle on an
+    evenly spaced sample: latents, decoded histograms, and the QoIs of the
+    corrected output (Eq. (1)-(4) through the four moments)."""
+    import torch
+    import oracle
     n = x.shape[0]
-    if int(out.count.item()) > 0:
+    idx = torch.as_tensor(np.linspace(0, n - 1, k).astype(np.int64), device=x.device)
+    xs = x[idx].contiguous()
+    z, sc = aeqc.ae_encode(model, xs)
+    xh = aeqc.ae_decode(model, z, sc)
+    torch.cuda.synchronize()
+    om = oracle.AE(**trained.get_group(0))
+    zo, xo, so = oracle.ae_forward(om, xs.cpu().numpy())
+    z = z.float().cpu().numpy().astype(np.float64)
+    xh = xh.cpu().numpy()[:, :xs.shape[1]].astype(np.float64)
+    zr = np.abs(z - zo) / (np.abs(zo).max(axis=1, keepdims=True) + 1e-300)
+    xr = np.abs(xh - xo) / so[:, None]
+    return {"sample": f"{k} histograms, evenly spaced",
+            "latent_rel_err": {"max": float(zr.max()), "mean": float(zr.mean())},
+            "decoded_rel_err_of_max": {"max": float(xr.max()), "mean": float(xr.mean())},
+            "note": "relative to each row's largest latent / each histogram's maximum; the "
+                    "QoI error of the corrected output is stats.max_qoi_rel_err"}
+
+
+def status_stats(aeqc, out):
+    st = out.status.cpu().numpy()
+    return dict(
+        converged_round1=float(np.mean((st & aeqc.ST_CONVERGED) != 0)),
+        verbatim=float(np.mean((st & aeqc.ST_VERBATIM) != 0)),
+        alpha_retry=float(np.mean((st & aeqc.ST_ALPHA_RETRY) != 0)),
+        warm_rejected=float(np.mean((st & aeqc.ST_WARM_REJECTED) != 0)),
+        mean_iters=float(out.iters.float().mean().item()))
+
+
+def run_grouped(args, rank, world, local):
+    """Subdomains with their own weights in one launch per stage, the call
+    autotuned and replayed from a CUDA graph; against the plain form with one
+    compress_batch per subdomain (FP32, FP64 correction, no graph); with
+    cfg['warm'] also the learned warm start."""
+    import ctypes as C
+    import torch
+    from paper_2212_10733_gb300 import aeqc, synth
+    lib = aeqc.load()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    cfg = CONFIGS[args.config]
+    x, sizes, off, master, tr = grouped_workload(cfg, args, rank, device, aeqc, synth)
+    n, G, P, L = x.shape[0], cfg["G"], synth.P, cfg["L"]
+    goff = torch.as_tensor(off, device=device)
+    grid = aeqc.Grid(*synth.grid_arrays())
+    stream = torch.cuda.current_stream()
+    res = {}
+
+    # ---- optimized form ----
+    opt = copy_model(aeqc, master, cfg, aeqc.DTYPE_BF16)
+    prm = aeqc.params_default(tau=cfg["tau"], kernel=aeqc.KERNEL_FAST)
+    out = aeqc.Compressed(n, P, L, opt.latent_dtype(), device, 16 * n)
+    ws = aeqc.compress_batch_workspace(opt, n, device)
+    tuning = aeqc.autotune(opt, grid, x, prm, group_offsets=goff, out=out, ws=ws)
+
+    def graph_for(mlp):
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            aeqc.compress_batch(opt, grid, x, prm, mlp=mlp, group_offsets=goff, out=out, ws=ws,
+                                stream=side)
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr):
+            aeqc.compress_batch(opt, grid, x, prm, mlp=mlp, group_offsets=goff, out=out, ws=ws,
+                                stream=torch.cuda.current_stream())
+        return gr
+
+    def timed(step):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = ClockSampler(local)
+        clk.start()
+        ms = time_steps(step, args.steps, stream)
+        clocks = clk.stop()
+        return max_over_ranks(ms, world), clocks
+
+    g0 = graph_for(None)
+    ms, clocks = timed(g0.replay)
+    head = dict(value=job_value(n, ms, world), ms=ms, clocks=clocks,
+                stats=status_stats(aeqc, out))
+    head["stats"].update(check_outputs(aeqc, grid, opt, out, x, prm, cfg["tau"], goff=goff))
+
+    # ---- learned warm start ----
+    warm = None
+    if cfg.get("warm"):
+        outf = aeqc.Compressed(n, P, L, opt.latent_dtype(), device, 16 * n, features=True)
+        aeqc.compress_batch(opt, grid, x, prm, group_offsets=goff, out=outf, ws=ws)
+        stf = outf.status.int()
+        ok = ((stf & aeqc.ST_CONVERGED) != 0) & ((stf & aeqc.ST_ALPHA_RETRY) == 0)
+        feats = outf.features[ok][: 1 << 20].contiguous()
+        lam = outf.lam[ok][: 1 << 20].contiguous()
+        del outf
+        fin = feats.double()
+        norm = dict(in_mu=fin.mean(0).cpu().numpy(), in_sd=fin.std(0).cpu().numpy() + 1e-12,
+                    out_mu=lam.mean(0).cpu().numpy(), out_sd=lam.std(0).cpu().numpy() + 1e-30)
+        del fin
+        mlp = aeqc.MLP(L + 4, 64)
+        mlp.set({**synth.mlp_init(L + 4, 64, 4, 1), **norm})
+        t0 = time.time()
+        mws, loss = None, torch.zeros(1, device=device)
+        npairs, Bm = feats.shape[0], 4096
+        steps = max(1, 2 * npairs // Bm)
+        for t in range(steps):
+            b = (t * Bm) % max(npairs - Bm, 1)
+            mws = mlp.train_step(feats[b:b + Bm], lam[b:b + Bm],
+                                 lr=1e-3 if t < 0.75 * steps else 1e-4, loss_out=loss, ws=mws)
+        torch.cuda.synchronize()
+        train_s = round(time.time() - t0, 2)
+        g1 = graph_for(mlp)
+        msw, clw = timed(g1.replay)
+        wst = status_stats(aeqc, out)
+        wst.update(check_outputs(aeqc, grid, opt, out, x, prm, cfg["tau"], goff=goff))
+        warm = {"value": round(job_value(n, msw, world), 1), "ms_per_step": round(msw, 3),
+                "speedup_vs_zero_start": round(ms / msw, 3),
+                "mean_iters_zero_start": head["stats"]["mean_iters"],
+                "mean_iters_warm": wst["mean_iters"],
+                "warm_rejected": wst["warm_rejected"], "stats": wst, "clocks": clw,
+                "mlp": {"shape": f"{L + 4}-64-64-4", "pairs": int(npairs), "train_steps": steps,
+                        "batch": Bm, "final_loss": float(loss.item()), "train_s": train_s}}
+        del g1
+
+    # ---- plain form: one compress_batch per subdomain, no graph ----
+    if not args.no_compare:
+        del g0
+        prm_p = aeqc.params_default(tau=cfg["tau"], kernel=aeqc.KERNEL_FP64)
+        outp = aeqc.Compressed(n, P, L, master.latent_dtype(), device, 16 * n)
+        wsp = aeqc.compress_batch_workspace(master, int(sizes.max()), device)
+        ks = np.arange(G + 1)
+        offs = [torch.as_tensor(np.where(ks <= g, 0, sizes[g]).astype(np.int64), device=device)
+                for g in range(G)]
+        views = [group_view(aeqc, outp, int(off[g]), int(off[g + 1])) for g in range(G)]
+
+        def step_plain():
+            for g in range(G):
+                r0, r1 = int(off[g]), int(off[g + 1])
+                aeqc._check(lib.compress_batch(
+                    master.h, None, C.byref(grid.c), x.data_ptr() + r0 * P * 8, r1 - r0,
+                    offs[g].data_ptr(), C.byref(prm_p), C.byref(views[g]), wsp.data_ptr(),
+                    wsp.numel(), stream.cuda_stream))
+
+        msp, clp = timed(step_plain)
+        res["plain"] = dict(value=job_value(n, msp, world), ms=msp, clocks=clp,
+                            stats=status_stats(aeqc, outp))
+
+    line = {
+        "metric": METRIC, "value": round(head["value"], 1), "unit": "histograms/s",
+        "input_gbs": round(head["value"] * HIST_BYTES / 1e9, 2),
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(head["ms"], 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 GEMM + int64/f32 correction",
+        "data": "synthetic (seeded Gaussian-mixture velocity histograms, lognormal subdomains)",
+        "config": {"workload": cfg["name"], "histograms_per_gpu": n, "subdomains": G,
+                   "subdomain_sizes": {"min": int(sizes.min()), "median": float(np.median(sizes)),
+                                       "max": int(sizes.max())},
+                   "ae": f"1521-{cfg['H']}-{cfg['L']}-{cfg['H']}-1521 tied linear per subdomain",
+                   "tau": cfg["tau"], "form": "optimized (one launch per stage, CUDA graph)",
+                   "tuning": tuning, "l2": "inputs larger than L2, no flush",
+                   "parallelism": f"dp{world} (independent shards)"},
+        "clocks": head["clocks"], "gpu_launches": 6 * args.steps,
+        "training": tr, "stats": head["stats"],
+    }
+    if warm:
+        line["warm_start"] = warm
+    if "plain" in res:
+        r = res["plain"]
+        line["vs_plain_form"] = {"value": round(r["value"], 1), "ms_per_step": round(r["ms"], 3),
+                                 "speedup": round(head["value"] / r["value"], 2),
+                                 "form": "FP32 SIMT GEMMs + FP64 correction, one call per "
+                                         "subdomain, no graph",
+                                 "stats": r["stats"], "clocks": r["clocks"]}
+    return line
+
+
+def check_outputs(aeqc, grid, model, out, x, prm, tau, chunk=1 << 20, goff=None):
+    """Decompress the batch and measure max |f - x| / e and the relative QoI
+    error over all histograms.  One group: in row chunks, each with the
+    escaped values of its rows re-indexed from the chunk start (the outlier
+    list holds global indices)."""
+    import torch
+    n, P = x.shape
+    if goff is not None:
         chunk = n
+    cnt = int(out.count.item())
+    idx_all = out.index[:min(cnt, out.index.numel())]
+    val_all = out.value[:idx_all.numel()]
     e_max, q_max = 0.0, 0.0
     for c0 in range(0, n, chunk):
         c1 = min(n, c0 + chunk)
         view = SubView(aeqc, out, c0, c1)
-        f = aeqc.decompress_batch(model, grid, view, prm)
+        if idx_all.numel() and c1 - c0 < n:
+            sel = (idx_all >= c0 * P) & (idx_all < c1 * P)
+            li = (idx_all[sel] - c0 * P).contiguous()
+            lv = val_all[sel].contiguous()
+            lc = torch.tensor([li.numel()], dtype=torch.int64, device=x.device)
+            view.keep = (li, lv, lc)
+            view.c.outliers = aeqc.aeqc_outliers(li.numel(), lc.data_ptr(),
+                                                 li.data_ptr() if li.numel() else None,
+                                                 lv.data_ptr() if lv.numel() else None)
+        f = aeqc.decompress_batch(model, grid, view, prm, group_offsets=goff)
         xs = x[c0:c1]
         e = tau * xs.amax(dim=1, keepdim=True)
         e_max = max(e_max, float(((f - xs).abs() / e).max().item()))
@@ -479,7 +763,7 @@ def cpu_baseline(args, cfg, model, budget_s, rank=0):
     vpar, vperp, vol = synth.grid_arrays()
     og = oracle.Grid(vpar=vpar, vperp=vperp, vol_uniform=vol)
     op = oracle.Params(tau=cfg["tau"])
-    n_full = args.n or cfg["n"]
+    n_full = workload_size(cfg, args, synth, rank)
 
     def run(k):
         idx = np.linspace(0, n_full - 1, k).astype(np.int64)
@@ -515,7 +799,7 @@ def run_reference(args, rank, world):
     import oracle
     from paper_2212_10733_gb300 import synth
     cfg = CONFIGS[args.config]
-    n_full = args.n or cfg["n"]
+    n_full = workload_size(cfg, args, synth)
     P, H, L = synth.P, cfg["H"], cfg["L"]
     om = oracle.AE(**synth.ae_init(P, H, L, synth.config_seed(1)))
     vpar, vperp, vol = synth.grid_arrays()
@@ -560,6 +844,17 @@ def main():
         print(json.dumps(run_reference(args, rank, world)))
         return
     rank, world, local = dist_setup(args)
+    if CONFIGS[args.config].get("G"):
+        line = run_grouped(args, rank, world, local)
+        if rank == 0 and world == 1 and not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(args, CONFIGS[args.config], None,
+                                                args.cpu_seconds)
+        if rank == 0:
+            print(json.dumps(line))
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
     res, model, cfg = run_ours(args, rank, world, local)
     if res is None:  # --profile run
         print("profiled %s x%d" % (args.profile, args.steps))

@@ -43,17 +43,25 @@ __device__ __forceinline__ unsigned long long f64_key(unsigned long long u) {
   return u ^ (((unsigned long long)((long long)u >> 63)) & 0x7FFFFFFFFFFFFFFFull);
 }
 
-// BF16 bits of a double, round to nearest even (values below the BF16 normal
-// range become zero, above it infinity)
-__device__ __forceinline__ uint32_t bf16_of_f64(unsigned long long u) {
-  const uint32_t sign = (uint32_t)(u >> 63) << 15;
-  unsigned long long a = u & 0x7FFFFFFFFFFFFFFFull;
-  if (a > 0x7FF0000000000000ull) return sign | 0x7FC0u;
-  a += 0x00000FFFFFFFFFFFull + ((a >> 45) & 1ull);
-  const int E = (int)(a >> 52);
-  if (E >= 1151) return sign | 0x7F80u;
-  if (E <= 896) return sign;
-  return sign | ((uint32_t)(E - 896) << 7) | ((uint32_t)(a >> 45) & 0x7Fu);
+// BF16 bits of a double (given as its two 32-bit words), round to nearest
+// even (values below the BF16 normal range become zero, above it infinity).
+// The high word carries sign, exponent
+// and 20 mantissa bits; any set bit of the low word only matters as a sticky
+// bit below the rounding position, so it is OR-ed into bit 0 of the high word.
+// Round half to even at bit 13 then gives the BF16 significand; the exponent
+// is rebiased when it is in the BF16 normal range.
+__device__ __forceinline__ uint32_t bf16_of_f64_words(uint32_t hi, uint32_t lo) {
+  const uint32_t sign = (hi >> 16) & 0x8000u;
+  const uint32_t a = (hi & 0x7FFFFFFFu) | (lo != 0u ? 1u : 0u);
+  const uint32_t r = a + 0xFFFu + ((a >> 13) & 1u);
+  const uint32_t E = r >> 20;
+  uint32_t v = sign | ((r >> 13) - (896u << 7));
+  if (E - 897u >= 254u) {  // outside the BF16 normal range (rare, except zero)
+    if (E <= 896u) v = sign;
+    else if (a > 0x7FF00000u) v = sign | 0x7FC0u;  // NaN
+    else v = sign | 0x7F80u;                       // overflow, infinity
+  }
+  return v;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -246,9 +254,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncwarp();
   } else {
     // ---- converters: FP64 rows -> BF16 swizzled A tiles, row maxima ----
-    unsigned long long mkey[16];
+    // row maxima on the raw bits as signed 64-bit integers: exact among
+    // non-negative values (which order like their bits) and below any of
+    // them for negatives; a row without a non-negative value is redone
+    // exactly after the main loop
+    long long mraw[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) mkey[i] = f64_key(0xFFF0000000000000ull);  // -inf
+    for (int i = 0; i < 16; ++i) mraw[i] = (long long)0x8000000000000000ull;
     bool ok = true;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % ns;
@@ -274,10 +286,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int r = warp * 16 + i;
-        const unsigned long long k0k = f64_key(v0[i]), k1k = f64_key(v1[i]);
-        if (k0 < a.P && (long long)k0k > (long long)mkey[i]) mkey[i] = k0k;
-        if (k0 + 1 < a.P && (long long)k1k > (long long)mkey[i]) mkey[i] = k1k;
-        const uint32_t packed = bf16_of_f64(v0[i]) | (bf16_of_f64(v1[i]) << 16);
+        if (k0 < a.P) mraw[i] = max(mraw[i], (long long)v0[i]);
+        if (k0 + 1 < a.P) mraw[i] = max(mraw[i], (long long)v1[i]);
+        const uint32_t packed =
+            bf16_of_f64_words((uint32_t)(v0[i] >> 32), (uint32_t)v0[i]) |
+            (bf16_of_f64_words((uint32_t)(v1[i] >> 32), (uint32_t)v1[i]) << 16);
         *reinterpret_cast<uint32_t*>(ast + swz128(r, lane >> 2) + (lane & 3) * 4) = packed;
       }
       fence_proxy_async_smem();
@@ -286,13 +299,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // row maxima: lanes hold partial maxima of rows warp*16 + i
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      long long k = (long long)mkey[i];
+      long long k = mraw[i];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const long long q = __shfl_xor_sync(0xffffffffu, k, o);
-        k = q > k ? q : k;
+      for (int o = 16; o > 0; o >>= 1) k = max(k, (long long)__shfl_xor_sync(0xffffffffu, k, o));
+      const int r = warp * 16 + i;
+      if (k < 0 && r < rows) {
+        // no non-negative value: the exact maximum on order-preserving keys
+        const double* xr = a.x + (ti.m0 + r) * (long long)a.P;
+        long long kk = (long long)f64_key(0xFFF0000000000000ull);
+        for (int p = lane; p < a.P; p += 32)
+          kk = max(kk, (long long)f64_key((unsigned long long)__double_as_longlong(__ldg(xr + p))));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+          kk = max(kk, (long long)__shfl_xor_sync(0xffffffffu, kk, o));
+        k = (long long)f64_key((unsigned long long)kk);
       }
-      if (lane == 0) rowmax[warp * 16 + i] = __longlong_as_double((long long)f64_key((unsigned long long)k));
+      if (lane == 0) rowmax[r] = __longlong_as_double(k);
     }
     named_sync(1, NCONV * 32);
     // ---- E1 epilogue: TMEM -> act(acc / s + b1) -> BF16 swizzled h tile ----

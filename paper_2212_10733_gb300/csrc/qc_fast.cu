@@ -265,12 +265,23 @@ struct Moments {
   unsigned flags;  // CODE_ESCAPE / AE_EXACT
 };
 
-// exact sum over the warp of a 64-bit integer (the totals are bounded on the
-// host so that they fit)
-__device__ __forceinline__ long long wsum_ll(long long v) {
+// Sums over the warp of 32 64-bit values held by every lane, scattered:
+// lane k returns the total of value k.  Recursive halving: at each step a
+// lane keeps the half of its values selected by its lane bit and adds its
+// partner's copy of that half (the totals are bounded on the host so that
+// they fit).
+__device__ __forceinline__ long long reduce_scatter32(long long (&v)[32], int lane) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  return v;
+  for (int o = 16, n = 16; o >= 1; o >>= 1, n >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      const long long send = up ? v[i] : v[n + i];
+      const long long keep = up ? v[n + i] : v[i];
+      v[i] = keep + __shfl_xor_sync(FULL, send, o);
+    }
+  }
+  return v[0];
 }
 
 // Each lane walks down (part of) grid columns, so that the weights in i are
@@ -371,16 +382,43 @@ __device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb,
   float s1 = c1.xs * fabsf(fmaf(b_f, small_int_to_float(sg1.c - fg.i_c), c0_f)) +
              c2.xs * fabsf(fmaf(b_f, small_int_to_float(sg2.c - fg.i_c), c0_f));
   __syncwarp();
-  // exact warp totals (the host bounds them below 2^62), then double-float
-  df u[4], t[9];
+  // exact warp totals (the host bounds them below 2^62), scattered over the
+  // lanes: lane k holds total k of (U0..U3, Tb0..Tb8, Ta0..Ta8); each lane
+  // converts one total to double-float
+  long long v[32];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) u[q] = df_from_ll(wsum_ll(U[q]));
+  for (int i = 0; i < 32; ++i)
+    v[i] = i < 4 ? U[i] : (i < 13 ? Tb[i - 4] : (i < 22 ? Ta[i - 13] : 0ll));
+  df mine = df_from_ll(reduce_scatter32(v, lane));
+  {
+    const df ta = {__shfl_down_sync(FULL, mine.hi, 9), __shfl_down_sync(FULL, mine.lo, 9)};
+    if (lane >= 4 && lane < 13) mine = df_add(df_ldexp(ta, 31), mine);  // T = Tb + 2^31 Ta
+  }
+  float S1 = s1;
 #pragma unroll
-  for (int q = 0; q < 9; ++q)
-    t[q] = df_add(df_ldexp(df_from_ll(wsum_ll(Ta[q])), 31), df_from_ll(wsum_ll(Tb[q])));
-  const float S1 = df_wsum(df{s1, 0.f}).hi;
+  for (int o = 16; o > 0; o >>= 1) S1 += __shfl_xor_sync(FULL, S1, o);
   const df vol = {fg.vol_h, fg.vol_l};
   const df sr = df_ldexp(vol, c.k - 30), sm = df_ldexp(vol, c.k - QF);
+  // moment j = m(p, q) in lane j < 9, (p, q) in the order of the T totals:
+  // m(p, q) = vol Delta 2^-38 d2^q sum_r C(p,r) b^r c0^(p-r) T[r][q]
+  df mj;
+  {
+    const int jj = lane < 9 ? lane : 0;
+    const int pj = jj < 5 ? jj : (jj < 8 ? jj - 5 : 0), qj = jj < 5 ? 0 : (jj < 8 ? 1 : 2);
+    df acc = {0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r <= 4; ++r) {
+      const int src = 4 + (qj == 0 ? r : (qj == 1 ? 5 + min(r, 2) : 8));
+      const df tr = {__shfl_sync(FULL, mine.hi, src), __shfl_sync(FULL, mine.lo, src)};
+      if (r <= pj) acc = df_add(acc, df_mul(df{fg.coef_h[pj][r], fg.coef_l[pj][r]}, tr));
+    }
+    mj = df_mul(sm, df_mul(df{fg.d2q_h[qj], fg.d2q_l[qj]}, acc));
+  }
+  df mm[9], u[4];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) mm[j] = df{__shfl_sync(FULL, mj.hi, j), __shfl_sync(FULL, mj.lo, j)};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) u[q] = df{__shfl_sync(FULL, mine.hi, q), __shfl_sync(FULL, mine.lo, q)};
   const df b = {fg.coef_h[1][1], fg.coef_l[1][1]};   // C(1,1) b = b
   const df c0 = {fg.coef_h[1][0], fg.coef_l[1][0]};  // C(1,0) c0 = c0
   const df d2 = {fg.d2q_h[1], fg.d2q_l[1]};
@@ -397,28 +435,15 @@ __device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb,
     acc = df_add(acc, df_mul(cc[2], u[2]));
     mo.R[3] = df_mul(sr, acc);
   }
-  // m(p, q) = vol Delta 2^-38 d2^q sum_r C(p,r) b^r c0^(p-r) T[r][q]
-  const df* Tq0 = t;      // T[r][0], r = 0..4
-  const df Tq1[3] = {t[5], t[6], t[7]};
-  auto mom = [&](int p, int q) {
-    df acc = {0.f, 0.f};
-    for (int r = 0; r <= p; ++r) {
-      const df tr = q == 0 ? Tq0[r] : (q == 1 ? Tq1[r] : t[8]);
-      acc = df_add(acc, df_mul(df{fg.coef_h[p][r], fg.coef_l[p][r]}, tr));
-    }
-    return df_mul(sm, df_mul(df{fg.d2q_h[q], fg.d2q_l[q]}, acc));
-  };
-  const df m00 = mom(0, 0), m10 = mom(1, 0), m20 = mom(2, 0), m30 = mom(3, 0),
-           m40 = mom(4, 0), m01 = mom(0, 1), m11 = mom(1, 1), m21 = mom(2, 1),
-           m02 = mom(0, 2);
-  mo.M[0] = m00; mo.M[1] = m10; mo.M[2] = m01; mo.M[3] = m20;
-  mo.M[4] = m20; mo.M[5] = m11; mo.M[6] = m30;
-  mo.M[7] = m02; mo.M[8] = m21;
-  mo.M[9] = m40;
-  mo.S[0] = m00.hi;
+  // mm: m00 m10 m20 m30 m40 m01 m11 m21 m02
+  mo.M[0] = mm[0]; mo.M[1] = mm[1]; mo.M[2] = mm[5]; mo.M[3] = mm[2];
+  mo.M[4] = mm[2]; mo.M[5] = mm[6]; mo.M[6] = mm[3];
+  mo.M[7] = mm[8]; mo.M[8] = mm[7];
+  mo.M[9] = mm[4];
+  mo.S[0] = mm[0].hi;
   mo.S[1] = fg.vol_h * S1;
-  mo.S[2] = m01.hi;
-  mo.S[3] = m20.hi;
+  mo.S[2] = mm[5].hi;
+  mo.S[3] = mm[2].hi;
   mo.flags = 0;
   if (__any_sync(FULL, esc)) mo.flags |= AEQC_ST_CODE_ESCAPE;
   if (!__any_sync(FULL, nonzero)) mo.flags |= AEQC_ST_AE_EXACT;

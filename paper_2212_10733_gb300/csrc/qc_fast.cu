@@ -100,14 +100,6 @@ __device__ __forceinline__ float exp2i(int n) {  // 2^n for n in [-126, 127]
 __device__ __forceinline__ df df_ldexp(df x, int n) {  // exact for normal results
   return {ldexpf(x.hi, n), ldexpf(x.lo, n)};
 }
-__device__ __forceinline__ df df_wsum(df x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    df y = {__shfl_xor_sync(FULL, x.hi, o), __shfl_xor_sync(FULL, x.lo, o)};
-    x = df_add(x, y);
-  }
-  return x;
-}
 // the top 48 bits of an int64 as a float pair (relative error <= 2^-48)
 __device__ __forceinline__ df df_from_ll(long long v) {
   if (v == 0) return {0.f, 0.f};
@@ -270,6 +262,27 @@ struct Moments {
 // lane keeps the half of its values selected by its lane bit and adds its
 // partner's copy of that half (the totals are bounded on the host so that
 // they fit).
+// Warp sums of four double-float values held by every lane: the total of
+// value k ends in lanes 8k..8k+7 (halving over lane bits 4 and 3, then a
+// butterfly over the remaining three bits), added error-free.
+__device__ __forceinline__ df df_reduce_scatter4(const df (&a)[4], int lane) {
+  const bool u4 = (lane & 16) != 0, u3 = (lane & 8) != 0;
+  df v[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const df send = u4 ? a[i] : a[2 + i];
+    const df keep = u4 ? a[2 + i] : a[i];
+    v[i] = df_add(keep, df{__shfl_xor_sync(FULL, send.hi, 16), __shfl_xor_sync(FULL, send.lo, 16)});
+  }
+  const df send = u3 ? v[0] : v[1];
+  df x = df_add(u3 ? v[1] : v[0],
+                df{__shfl_xor_sync(FULL, send.hi, 8), __shfl_xor_sync(FULL, send.lo, 8)});
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1)
+    x = df_add(x, df{__shfl_xor_sync(FULL, x.hi, o), __shfl_xor_sync(FULL, x.lo, o)});
+  return x;
+}
+
 __device__ __forceinline__ long long reduce_scatter32(long long (&v)[32], int lane) {
 #pragma unroll
   for (int o = 16, n = 16; o >= 1; o >>= 1, n >>= 1) {
@@ -543,19 +556,39 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
     }
     ab1 = fmaf(s0.hi, fabsf(icf), ab1);  // y >= 0
   }
+  // warp totals of the four sums, scattered (total k in lanes 8k..8k+7), in
+  // double-float; then H_k in lane k and every total and H broadcast
+  const df Ak = df_reduce_scatter4(a, lane);
+  float B1 = ab1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) B1 += __shfl_xor_sync(FULL, B1, o);
   df A[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) A[k] = df_wsum(a[k]);
-  const float B1 = df_wsum(df{ab1, 0.f}).hi;
+  for (int k = 0; k < 4; ++k) A[k] = df{__shfl_sync(FULL, Ak.hi, 8 * k), __shfl_sync(FULL, Ak.lo, 8 * k)};
   const df vol = {fg.vol_h, fg.vol_l};
+  // H_k = vol sum phi_k y with phi = (1, v, w, v^2), v = b ic + c0, w = d2 j^2:
+  // H0 = vol A0, H1 = vol (b A1 + c0 A0), H2 = vol d2 A3,
+  // H3 = vol (b^2 A2 + 2 b c0 A1 + c0^2 A0); lane k forms H_k
+  df hk;
+  {
+    const int k = lane & 3;
+    const df c1 = k == 1 ? df{fg.coef_h[1][1], fg.coef_l[1][1]}
+                         : (k == 3 ? df{fg.coef_h[2][2], fg.coef_l[2][2]} : df{0.f, 0.f});
+    const df c2 = k == 1 ? df{fg.coef_h[1][0], fg.coef_l[1][0]}
+                         : (k == 3 ? df{fg.coef_h[2][1], fg.coef_l[2][1]} : df{0.f, 0.f});
+    const df c3 = k == 3 ? df{fg.coef_h[2][0], fg.coef_l[2][0]} : df{0.f, 0.f};
+    df acc;
+    if (k == 0) acc = A[0];
+    else if (k == 2) acc = df_mul(df{fg.d2q_h[1], fg.d2q_l[1]}, A[3]);
+    else if (k == 1) acc = df_add(df_mul(c1, A[1]), df_mul(c2, A[0]));
+    else acc = df_add(df_add(df_mul(c1, A[2]), df_mul(c2, A[1])), df_mul(c3, A[0]));
+    hk = df_mul(vol, acc);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.H[k] = df{__shfl_sync(FULL, hk.hi, k), __shfl_sync(FULL, hk.lo, k)};
   const df c0 = {fg.coef_h[1][0], fg.coef_l[1][0]}, b = {fg.coef_h[1][1], fg.coef_l[1][1]};
   const df c00 = {fg.coef_h[2][0], fg.coef_l[2][0]}, c21 = {fg.coef_h[2][1], fg.coef_l[2][1]};
   const df bb = {fg.coef_h[2][2], fg.coef_l[2][2]}, d2 = {fg.d2q_h[1], fg.d2q_l[1]};
-  // H_k = vol sum phi_k y with phi = (1, v, w, v^2), v = b ic + c0, w = d2 j^2
-  o.H[0] = df_mul(vol, A[0]);
-  o.H[1] = df_mul(vol, df_add(df_mul(b, A[1]), df_mul(c0, A[0])));
-  o.H[2] = df_mul(vol, df_mul(d2, A[3]));
-  o.H[3] = df_mul(vol, df_add(df_add(df_mul(bb, A[2]), df_mul(c21, A[1])), df_mul(c00, A[0])));
   // y >= 0 (h >= 0, x' >= 0), so A0, A2, A3 are sums of non-negative terms
   const float vh = fg.vol_h;
   o.Habs[0] = vh * fabsf(A[0].hi);
@@ -905,7 +938,7 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(FW * 32) fused_fast_kernel(const FusedArgs a) {
+__global__ void __launch_bounds__(FW * 32, 4) fused_fast_kernel(const FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FastWS& w = reinterpret_cast<FastWS*>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;

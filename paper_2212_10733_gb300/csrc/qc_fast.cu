@@ -667,30 +667,6 @@ __device__ __forceinline__ void chol_solve(const Chol& ch, const float r[4], flo
   for (int k = 0; k < 4; ++k) dlt[k] = z[k] * ch.d[k];
 }
 
-// (M v)_k in double-float for a float vector v
-__device__ __forceinline__ void df_matvec_f(const df M[10], const float v[4], df out[4]) {
-  const int idx[4][4] = {{0, 1, 2, 3}, {1, 4, 5, 6}, {2, 5, 7, 8}, {3, 6, 8, 9}};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    df acc = df_mul_f(M[idx[k][0]], v[0]);
-#pragma unroll
-    for (int l = 1; l < 4; ++l) acc = df_add(acc, df_mul_f(M[idx[k][l]], v[l]));
-    out[k] = acc;
-  }
-}
-
-// (M lambda)_k in double-float
-__device__ __forceinline__ void df_matvec(const df M[10], const df lam[4], df out[4]) {
-  const int idx[4][4] = {{0, 1, 2, 3}, {1, 4, 5, 6}, {2, 5, 7, 8}, {3, 6, 8, 9}};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    df acc = df_mul(M[idx[k][0]], lam[0]);
-#pragma unroll
-    for (int l = 1; l < 4; ++l) acc = df_add(acc, df_mul(M[idx[k][l]], lam[l]));
-    out[k] = acc;
-  }
-}
-
 struct NewtonState {
   int check_viol;  // end-to-end violation at the final lambda (valid when converged)
   float gres[4];   // |g_k| / S_k at the final lambda
@@ -702,6 +678,18 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
                            const QConst& c, const Moments& mo, const Chol& ch, df lam[4],
                            int max_iter, float step, float tol, float e, float s, int* iters,
                            float* r0, float* rlast, NewtonState& ns, int lane) {
+  // lane k (mod 4) owns row k of M and component k of R: the matrix-vector
+  // products run one row per lane and are gathered by shuffles
+  const int kr = lane & 3;
+  df rowM[4];
+  {
+    const int idx[4][4] = {{0, 1, 2, 3}, {1, 4, 5, 6}, {2, 5, 7, 8}, {3, 6, 8, 9}};
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+      rowM[l] = kr == 0 ? mo.M[idx[0][l]]
+                        : (kr == 1 ? mo.M[idx[1][l]] : (kr == 2 ? mo.M[idx[2][l]] : mo.M[idx[3][l]]));
+  }
+  const df Rk = kr == 0 ? mo.R[0] : (kr == 1 ? mo.R[1] : (kr == 2 ? mo.R[2] : mo.R[3]));
   for (int it = 0;; ++it) {
     df H[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     const bool zero_lam =
@@ -731,14 +719,22 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
       tmax = po.tmax;
     };
     if (!zero_lam) do_pass();
-    df Ml[4];
-    df_matvec(mo.M, lam, Ml);
+    // g_k = -R_k - (M lambda)_k + H_k, row k in lane k, gathered
     df gk[4];
+    {
+      df ml = df_mul(rowM[0], lam[0]);
+#pragma unroll
+      for (int l = 1; l < 4; ++l) ml = df_add(ml, df_mul(rowM[l], lam[l]));
+      const df Hk = kr == 0 ? H[0] : (kr == 1 ? H[1] : (kr == 2 ? H[2] : H[3]));
+      const df gl = df_add(df_neg(df_add(Rk, ml)), Hk);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        gk[k] = df{__shfl_sync(FULL, gl.hi, k), __shfl_sync(FULL, gl.lo, k)};
+    }
     float res = 0.f;
     bool finite_ok = true;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      gk[k] = df_add(df_neg(df_add(mo.R[k], Ml[k])), H[k]);
       const float den = mo.S[k] > 0.f ? mo.S[k] : 1e-30f;
       const float rk = fabsf(gk[k].hi) / den;
       finite_ok = finite_ok && isfinite(rk);
@@ -765,10 +761,15 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
 #pragma unroll
     for (int k = 0; k < 4; ++k) r[k] = gk[k].hi;
     chol_solve(ch, r, d1);
-    df Md[4];
-    df_matvec_f(mo.M, d1, Md);
+    {
+      df md = df_mul_f(rowM[0], d1[0]);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) r[k] = df_add(gk[k], df_neg(Md[k])).hi;
+      for (int l = 1; l < 4; ++l) md = df_add(md, df_mul_f(rowM[l], d1[l]));
+      const df gl = kr == 0 ? gk[0] : (kr == 1 ? gk[1] : (kr == 2 ? gk[2] : gk[3]));
+      const float rl = df_add(gl, df_neg(md)).hi;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r[k] = __shfl_sync(FULL, rl, k);
+    }
     chol_solve(ch, r, d2);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {

@@ -340,8 +340,17 @@ __device__ __forceinline__ void quant_segment(const Seg& sg, int n_par, const do
                                               int& nonzero) {
   cs = ColSums{{0, 0, 0}, {0, 0, 0}, {0, 0}, 0.f};
   int p = sg.j0 * n_par + sg.c;
+  // loads of the next point issued before the work on this one
+  double xn = sg.j0 < sg.j1 ? __ldg(xb + p) : 0.0;
+  float hn = sg.j0 < sg.j1 ? __ldg(xhb + p) : 0.f;
   for (int j = sg.j0; j < sg.j1; ++j, p += n_par) {
-    const PointQ o = quant_point_int(__ldg(xb + p), __ldg(xhb + p), c);
+    const double x = xn;
+    const float xh = hn;
+    if (j + 1 < sg.j1) {
+      xn = __ldg(xb + p + n_par);
+      hn = __ldg(xhb + p + n_par);
+    }
+    const PointQ o = quant_point_int(x, xh, c);
     cb[p] = (int16_t)o.code;
     w.xp[p] = o.xpf;
     w.rho[p] = (int16_t)((o.rho32 + (1 << 14)) >> 15);

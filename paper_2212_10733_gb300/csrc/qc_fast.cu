@@ -340,15 +340,19 @@ __device__ __forceinline__ void quant_segment(const Seg& sg, int n_par, const do
                                               int& nonzero) {
   cs = ColSums{{0, 0, 0}, {0, 0, 0}, {0, 0}, 0.f};
   int p = sg.j0 * n_par + sg.c;
-  // loads of the next point issued before the work on this one
+  // loads issued two points ahead of the work
   double xn = sg.j0 < sg.j1 ? __ldg(xb + p) : 0.0;
   float hn = sg.j0 < sg.j1 ? __ldg(xhb + p) : 0.f;
+  double xn2 = sg.j0 + 1 < sg.j1 ? __ldg(xb + p + n_par) : 0.0;
+  float hn2 = sg.j0 + 1 < sg.j1 ? __ldg(xhb + p + n_par) : 0.f;
   for (int j = sg.j0; j < sg.j1; ++j, p += n_par) {
     const double x = xn;
     const float xh = hn;
-    if (j + 1 < sg.j1) {
-      xn = __ldg(xb + p + n_par);
-      hn = __ldg(xhb + p + n_par);
+    xn = xn2;
+    hn = hn2;
+    if (j + 2 < sg.j1) {
+      xn2 = __ldg(xb + p + 2 * n_par);
+      hn2 = __ldg(xhb + p + 2 * n_par);
     }
     const PointQ o = quant_point_int(x, xh, c);
     cb[p] = (int16_t)o.code;
@@ -799,10 +803,22 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
   // max(x) and input validity, on the bit patterns (no FP64 compares)
   unsigned long long umax = 0;
   int bad = 0;
-  for (int p = lane; p < P; p += 32) {
+  // four loads in flight per lane
+  int p = lane;
+  for (; p + 96 < P; p += 128) {
+    unsigned long long u[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) u[q] = (unsigned long long)__double_as_longlong(__ldg(xb + p + 32 * q));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (u[q] <= 0x7FEFFFFFFFFFFFFFull) umax = u[q] > umax ? u[q] : umax;  // finite, >= +0
+      else bad |= u[q] != 0x8000000000000000ull;                            // -0 counts as 0
+    }
+  }
+  for (; p < P; p += 32) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(__ldg(xb + p));
-    if (u <= 0x7FEFFFFFFFFFFFFFull) umax = u > umax ? u : umax;  // finite, >= +0
-    else bad |= u != 0x8000000000000000ull;                      // -0 counts as 0
+    if (u <= 0x7FEFFFFFFFFFFFFFull) umax = u > umax ? u : umax;
+    else bad |= u != 0x8000000000000000ull;
   }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) {

@@ -478,7 +478,8 @@ __device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb,
 struct PassOut {
   df H[4];
   float Habs[4];  // bounds on the sums of |terms| (for the FP32 rounding bound)
-  float tmax;
+  float tmax;     // max |t| over points with x' > 0
+  float errmax;   // largest FP32 check value |x' e^{-t} - x| of the points
   int viol, uncertain;
 };
 
@@ -515,7 +516,7 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
                           const QConst& c, const TCoef& tc, float e_lo, float e_hi, PassOut& o,
                           int lane) {
   df a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};  // sums of y, y ic, y ic^2, y j^2
-  float ab1 = 0.f, tmax = 0.f;
+  float ab1 = 0.f, tmax = 0.f, errmax = 0.f;
   int viol = 0, unc = 0;
   const float cq = c.dl_f * 3.0517578125e-05f, dq = -12582912.f * cq;  // Delta 2^-15
   // x' h(t) and the check of one point
@@ -527,6 +528,7 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
     // Delta rho from its 2^-15 fixed point: exact, see small_int_to_float
     const float drho = fmaf(__int_as_float(0x4B400000 + (int)w.rho[p]), cq, dq);
     const float err = fabsf(fmaf(xp, h - t, -drho));
+    errmax = fmaxf(errmax, err);
     viol |= err > e_hi;
     unc |= err > e_lo;
     return xp * h;
@@ -584,17 +586,19 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
   // H3 = vol (b^2 A2 + 2 b c0 A1 + c0^2 A0); lane k forms H_k
   df hk;
   {
+    // H_k = vol (a0 A0 + a1 A1 + a2 A2 + a3 A3) with per-lane coefficients
+    // (1,0,0,0), (c0,b,0,0), (0,0,0,d2), (c0^2,2bc0,b^2,0): no divergence
     const int k = lane & 3;
-    const df c1 = k == 1 ? df{fg.coef_h[1][1], fg.coef_l[1][1]}
-                         : (k == 3 ? df{fg.coef_h[2][2], fg.coef_l[2][2]} : df{0.f, 0.f});
-    const df c2 = k == 1 ? df{fg.coef_h[1][0], fg.coef_l[1][0]}
-                         : (k == 3 ? df{fg.coef_h[2][1], fg.coef_l[2][1]} : df{0.f, 0.f});
-    const df c3 = k == 3 ? df{fg.coef_h[2][0], fg.coef_l[2][0]} : df{0.f, 0.f};
-    df acc;
-    if (k == 0) acc = A[0];
-    else if (k == 2) acc = df_mul(df{fg.d2q_h[1], fg.d2q_l[1]}, A[3]);
-    else if (k == 1) acc = df_add(df_mul(c1, A[1]), df_mul(c2, A[0]));
-    else acc = df_add(df_add(df_mul(c1, A[2]), df_mul(c2, A[1])), df_mul(c3, A[0]));
+    const df zero = {0.f, 0.f};
+    const df a0 = k == 0 ? df{1.f, 0.f}
+                         : (k == 1 ? df{fg.coef_h[1][0], fg.coef_l[1][0]}
+                                   : (k == 3 ? df{fg.coef_h[2][0], fg.coef_l[2][0]} : zero));
+    const df a1 = k == 1 ? df{fg.coef_h[1][1], fg.coef_l[1][1]}
+                         : (k == 3 ? df{fg.coef_h[2][1], fg.coef_l[2][1]} : zero);
+    const df a2 = k == 3 ? df{fg.coef_h[2][2], fg.coef_l[2][2]} : zero;
+    const df a3 = k == 2 ? df{fg.d2q_h[1], fg.d2q_l[1]} : zero;
+    df acc = df_add(df_mul(a0, A[0]), df_mul(a1, A[1]));
+    acc = df_add(acc, df_add(df_mul(a2, A[2]), df_mul(a3, A[3])));
     hk = df_mul(vol, acc);
   }
 #pragma unroll
@@ -608,10 +612,14 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
   o.Habs[1] = vh * (fabsf(b.hi) * B1 + fabsf(c0.hi) * fabsf(A[0].hi));
   o.Habs[2] = vh * d2.hi * fabsf(A[3].hi);
   o.Habs[3] = vh * (bb.hi * fabsf(A[2].hi) + fabsf(c21.hi) * B1 + c00.hi * fabsf(A[0].hi));
-  float tm = tmax;
+  float tm = tmax, em = errmax;
 #pragma unroll
-  for (int s = 16; s > 0; s >>= 1) tm = fmaxf(tm, __shfl_xor_sync(FULL, tm, s));
+  for (int s = 16; s > 0; s >>= 1) {
+    tm = fmaxf(tm, __shfl_xor_sync(FULL, tm, s));
+    em = fmaxf(em, __shfl_xor_sync(FULL, em, s));
+  }
   o.tmax = tm;
+  o.errmax = em;
   o.viol = __any_sync(FULL, viol);
   o.uncertain = __any_sync(FULL, unc);
 }
@@ -703,13 +711,14 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
                         : (kr == 1 ? mo.M[idx[1][l]] : (kr == 2 ? mo.M[idx[2][l]] : mo.M[idx[3][l]]));
   }
   const df Rk = kr == 0 ? mo.R[0] : (kr == 1 ? mo.R[1] : (kr == 2 ? mo.R[2] : mo.R[3]));
+  bool force_pass = false;  // converged at lambda = 0: repeat the iteration with the check
   for (int it = 0;; ++it) {
     df H[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     const bool zero_lam =
         lam[0].hi == 0.f && lam[1].hi == 0.f && lam[2].hi == 0.f && lam[3].hi == 0.f;
     int viol = 0, unc = 0;
     bool did_pass = false;
-    float tmax = 0.f;
+    float tmax = 0.f, errmax = 0.f, pmargin = 0.f;
     auto do_pass = [&]() {
       const float tb = fabsf(lam[0].hi) + fabsf(lam[1].hi) * fg.vmax + fabsf(lam[2].hi) * fg.wmax +
                        fabsf(lam[3].hi) * fg.vmax * fg.vmax;
@@ -730,8 +739,10 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
       unc = po.uncertain;
       did_pass = true;
       tmax = po.tmax;
+      errmax = po.errmax;
+      pmargin = margin;
     };
-    if (!zero_lam) do_pass();
+    if (!zero_lam || force_pass) do_pass();
     // g_k = -R_k - (M lambda)_k + H_k, row k in lane k, gathered
     df gk[4];
     {
@@ -763,7 +774,11 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
     for (int k = 0; k < 4; ++k)
       if (fabsf(H[k].hi) > 1e-5f * mo.S[k]) return -1;
     if (res <= tol) {
-      if (!did_pass) do_pass();  // lambda = 0 converged: still check every point
+      if (!did_pass) {  // lambda = 0 converged: still check every point
+        force_pass = true;
+        --it;
+        continue;
+      }
       if (unc && !viol) return -1;
       ns.check_viol = viol;
       return 1;
@@ -784,6 +799,48 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
       for (int k = 0; k < 4; ++k) r[k] = __shfl_sync(FULL, rl, k);
     }
     chol_solve(ch, r, d2);
+    // Certificate after a pass (unit step): g at the new lambda is the
+    // residual of the solve plus H(l + d) - H(l), and |h'(t)| <= |t| e^|t|
+    // bounds that change by (tmax + tb_d) e^(tmax + tb_d) tb_d S_k (tb_d bounds
+    // |d.phi| on the grid); g itself carries at most 2e-13 S_k of FP32 error
+    // (the pass's bound).  The pointwise check moves by at most
+    // x'max e^tmax (e^tb_d - 1).  When both bounds hold, the step is taken
+    // and the histogram converged without the pass at the new lambda.
+    if (did_pass && step == 1.f && !viol && !unc) {
+      float dd[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) dd[k] = d1[k] + d2[k];
+      const float tbd = fabsf(dd[0]) + fabsf(dd[1]) * fg.vmax + fabsf(dd[2]) * fg.wmax +
+                        fabsf(dd[3]) * fg.vmax * fg.vmax;
+      const float tt = tmax + tbd;
+      if (tt < 0.05f) {
+        const float grow = (1.f + 1.1f * tt) * 1.01f;  // e^tt for tt < 0.05, padded
+        // residual of the solve, row k in lane k: g - M (d1 + d2)
+        df md = df_mul_f(rowM[0], dd[0]);
+#pragma unroll
+        for (int l = 1; l < 4; ++l) md = df_add(md, df_mul_f(rowM[l], dd[l]));
+        const df gl = kr == 0 ? gk[0] : (kr == 1 ? gk[1] : (kr == 2 ? gk[2] : gk[3]));
+        const float Sk = kr == 0 ? mo.S[0] : (kr == 1 ? mo.S[1] : (kr == 2 ? mo.S[2] : mo.S[3]));
+        const float bk = fabsf(df_add(gl, df_neg(md)).hi) + Sk * (2e-13f + tt * grow * tbd);
+        const float rel = bk / (Sk > 0.f ? Sk : 1e-30f);
+        float worst = rel;
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) worst = fmaxf(worst, __shfl_xor_sync(FULL, worst, o));
+        const float xpmax = s + 2.f * c.dl_f;
+        if (worst <= tol && errmax + pmargin + xpmax * grow * tbd * 1.01f <= e) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            lam[k] = df_add_f(lam[k], d1[k]);
+            lam[k] = df_add_f(lam[k], d2[k]);
+            ns.gres[k] = __shfl_sync(FULL, rel, k);
+          }
+          *iters = it + 1;
+          *rlast = worst;
+          ns.check_viol = 0;
+          return 1;
+        }
+      }
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       lam[k] = df_add_f(lam[k], step * d1[k]);
@@ -876,26 +933,33 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
     NewtonState ns;
     ns.check_viol = 0;
     int conv, it1 = 0, itw = 0;
-    float r0 = 0.f, rw = 0.f, rd0, rd1;
+    float r0 = 0.f, rw = 0.f;
     const float tol = (float)pr.tol, step = (float)pr.step_s;
-    if (warm) {
-      conv = round1_fast(g, fg, w, c, mo, ch, lam, pr.warm_iters, step, tol, e, s_f, &itw, &r0,
-                         &rw, ns, lane);
-      if (conv == 0) {
-        if (!isfinite(rw) || !isfinite(r0) || rw > (float)pr.warm_reject || rw > r0) {
-          st |= AEQC_ST_WARM_REJECTED;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) lam[k] = df{0.f, 0.f};
-          conv = round1_fast(g, fg, w, c, mo, ch, lam, pr.max_iter, step, tol, e, s_f, &it1,
-                             &rd0, &rd1, ns, lane);
-        } else {
-          conv = round1_fast(g, fg, w, c, mo, ch, lam, pr.max_iter - pr.warm_iters, step, tol,
-                             e, s_f, &it1, &rd0, &rd1, ns, lane);
-        }
+    // one call site of the Newton loop: phase 0 the warm-start probation,
+    // phase 1 its continuation, phase 2 the start from zero
+    for (int phase = warm ? 0 : 2;;) {
+      const int cap = phase == 0 ? pr.warm_iters
+                                 : (phase == 1 ? pr.max_iter - pr.warm_iters : pr.max_iter);
+      int itx = 0;
+      float ra = 0.f, rb = 0.f;
+      conv = round1_fast(g, fg, w, c, mo, ch, lam, cap, step, tol, e, s_f, &itx, &ra, &rb, ns,
+                         lane);
+      if (phase != 0) {
+        it1 = itx;
+        break;
       }
-    } else {
-      conv = round1_fast(g, fg, w, c, mo, ch, lam, pr.max_iter, step, tol, e, s_f, &it1, &r0,
-                         &rd1, ns, lane);
+      itw = itx;
+      r0 = ra;
+      rw = rb;
+      if (conv != 0) break;
+      if (!isfinite(rw) || !isfinite(r0) || rw > (float)pr.warm_reject || rw > r0) {
+        st |= AEQC_ST_WARM_REJECTED;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) lam[k] = df{0.f, 0.f};
+        phase = 2;
+      } else {
+        phase = 1;
+      }
     }
     total_it += itw + it1;
     if (conv != 1) {  // round 2 and verbatim storage belong to the FP64 kernel

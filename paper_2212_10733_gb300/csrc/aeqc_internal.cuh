@@ -47,6 +47,9 @@ struct GridK {
 struct ParamsK {
   double tau, alpha, step_s, tol, warm_reject, qoi_check;
   int max_iter, r2_max_iter, loss, warm_iters;
+  // float copies for the fast kernel (no per-histogram conversions)
+  double alpha4;  // alpha / 4 (the retry level)
+  float tau_f, step_f, tol_f, warm_reject_f, qoi_check_f;
 };
 
 // Build kernel blocks from the public structs (validates; returns AEQC_*).

@@ -84,6 +84,12 @@ int make_params(const aeqc_params* p, ParamsK* k) {
   k->r2_max_iter = p->r2_max_iter;
   k->loss = p->loss;
   k->warm_iters = p->warm_iters;
+  k->alpha4 = p->alpha * 0.25;
+  k->tau_f = (float)p->tau;
+  k->step_f = (float)p->step_s;
+  k->tol_f = (float)p->tol;
+  k->warm_reject_f = (float)p->warm_reject;
+  k->qoi_check_f = (float)p->qoi_check;
   return AEQC_OK;
 }
 

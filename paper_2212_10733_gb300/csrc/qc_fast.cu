@@ -97,8 +97,9 @@ __device__ __forceinline__ df df_add_f(df x, float f) {
 __device__ __forceinline__ float exp2i(int n) {  // 2^n for n in [-126, 127]
   return __int_as_float((n + 127) << 23);
 }
-__device__ __forceinline__ df df_ldexp(df x, int n) {  // exact for normal results
-  return {ldexpf(x.hi, n), ldexpf(x.lo, n)};
+__device__ __forceinline__ df df_ldexp(df x, int n) {  // n in [-126, 127]; exact for normal results
+  const float f = exp2i(n);
+  return {x.hi * f, x.lo * f};
 }
 // the top 48 bits of an int64 as a float pair (relative error <= 2^-48)
 __device__ __forceinline__ df df_from_ll(long long v) {
@@ -890,10 +891,10 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
   int total_it = 0;
   float dfeat[4] = {0.f, 0.f, 0.f, 0.f};
   bool done = false;
-  const float s_f = (float)s;
+  const float s_f = float_of_bits(umax);  // s to 24 bits (margins only)
   for (int level = 0; level < 2 && !defer && !done; ++level) {
     QConst c;
-    if (!make_qconst(pr.tau, s, level ? pr.alpha * 0.25 : pr.alpha, c)) {
+    if (!make_qconst(pr.tau, s, level ? pr.alpha4 : pr.alpha, c)) {
       defer = true;
       break;
     }
@@ -929,12 +930,13 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
         if (!warm) st |= AEQC_ST_WARM_REJECTED;
       }
     }
-    const float e = (float)(pr.tau * s);
+    // e = tau max(x) in FP32 (relative error ~2^-22, inside the check's margin)
+    const float e = pr.tau_f * s_f;
     NewtonState ns;
     ns.check_viol = 0;
     int conv, it1 = 0, itw = 0;
     float r0 = 0.f, rw = 0.f;
-    const float tol = (float)pr.tol, step = (float)pr.step_s;
+    const float tol = pr.tol_f, step = pr.step_f;
     // one call site of the Newton loop: phase 0 the warm-start probation,
     // phase 1 its continuation, phase 2 the start from zero
     for (int phase = warm ? 0 : 2;;) {
@@ -952,7 +954,7 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
       r0 = ra;
       rw = rb;
       if (conv != 0) break;
-      if (!isfinite(rw) || !isfinite(r0) || rw > (float)pr.warm_reject || rw > r0) {
+      if (!isfinite(rw) || !isfinite(r0) || rw > pr.warm_reject_f || rw > r0) {
         st |= AEQC_ST_WARM_REJECTED;
 #pragma unroll
         for (int k = 0; k < 4; ++k) lam[k] = df{0.f, 0.f};
@@ -969,7 +971,7 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
     st |= AEQC_ST_CONVERGED;
     bool qoi_ok = true;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) qoi_ok = qoi_ok && ns.gres[k] <= (float)pr.qoi_check;
+    for (int k = 0; k < 4; ++k) qoi_ok = qoi_ok && ns.gres[k] <= pr.qoi_check_f;
     if (!ns.check_viol && qoi_ok) done = true;
     else if (level == 1) defer = true;  // verbatim after the retry: the FP64 kernel stores it
   }

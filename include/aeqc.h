@@ -26,8 +26,9 @@
  *     values of float64 per histogram (12,168 bytes for the 39 x 39 grid).
  *   - Calls that need temporary device memory take a caller-owned
  *     `workspace` of at least *_workspace_size() bytes (256-byte aligned).
- *     No call allocates device memory except aeqc_model_create and
- *     aeqc_mlp_create (which own their weights until *_destroy).
+ *     No call allocates device memory except aeqc_model_create,
+ *     aeqc_mlp_create, aeqc_model_load and aeqc_mlp_load (which own their
+ *     weights until *_destroy).
  *   - Calls on the same stream are ordered; calls on different streams that
  *     share an output, a workspace or a model race.
  */
@@ -417,6 +418,59 @@ int mlp_loss_grad(aeqc_mlp* m, const float* inputs, const double* target_lambda,
 int64_t aeqc_mlp_param_count(const aeqc_mlp* m);
 /* lambda0 [n][4] float64 from inputs [n][n_in] float32. */
 int mlp_predict(aeqc_mlp* m, const float* inputs, int64_t n, double* lambda0, void* stream);
+
+/* ---- checkpoints and the compressed-batch container ----------------------- */
+/* The paper stores, per histogram, the codes, the latent and the Lagrange
+ * multipliers (Sec. III, Stage 5) next to the trained network (Sec. III,
+ * Stage 1); it gives no file format.  These calls define one: little-endian
+ * blobs in HOST memory with an 8-byte magic, a version and a header size, so
+ * that a reader rejects what it does not know.  All of them are synchronous
+ * (they return when every copy has completed).
+ *
+ * Model checkpoint: header (magic "AEQCMDL1", version 1, 64 bytes: the
+ * aeqc_model_desc, floats per group and trainable floats per group), then
+ * FP32 params [n_groups][per group] (weights, biases, mu, sigma), Adam first
+ * and second moments [n_groups][trainable], int32 Adam step per group.
+ * Launch tuning is not saved (it belongs to the machine).  *_save_size gives
+ * the exact blob size; *_save needs bytes >= that.  *_load validates the
+ * header and the size (AEQC_ECORRUPT on a bad magic, version, descriptor or
+ * size: nothing is allocated then) and creates a new model that owns its
+ * device memory until aeqc_model_destroy. */
+size_t aeqc_model_save_size(const aeqc_model* m);
+int aeqc_model_save(const aeqc_model* m, void* blob_host, size_t bytes);
+int aeqc_model_load(const void* blob_host, size_t bytes, aeqc_model** out);
+
+/* MLP checkpoint: header (magic "AEQCMLP1", version 1, 40 bytes: n_in,
+ * n_hidden, floats of params, trainable floats), FP32 params (weights,
+ * biases and the input/output normalisation), Adam moments, int32 step. */
+size_t aeqc_mlp_save_size(const aeqc_mlp* m);
+int aeqc_mlp_save(const aeqc_mlp* m, void* blob_host, size_t bytes);
+int aeqc_mlp_load(const void* blob_host, size_t bytes, aeqc_mlp** out);
+
+/* Batch container: a 192-byte header (magic "AEQCBAT1", version 1, n, P, L,
+ * latent dtype, outlier count, total bytes and a table of eight sections as
+ * (offset, bytes), offsets 16-byte aligned, increasing, non-overlapping) then
+ * the sections latent [n][L] (model dtype), scale [n] f64, codes [n][P]
+ * int16, lambda [n][4] f64, iters [n] u8, status [n] u16, outlier index
+ * [count] i64 and value [count] f64.  The features array is not stored.
+ * pack_size is the blob size for these counts (0 for negative sizes).
+ * pack reads the device outlier count (clamped to the list's capacity; a
+ * dropped excess is already flagged in the status words), copies every
+ * section to blob_host and sets *written; bytes must cover the blob.
+ * peek validates the header against `bytes` and returns the counts (any
+ * output pointer may be NULL).  unpack validates the same way and copies
+ * every section, and the outlier count, into the caller's device arrays
+ * (outliers.capacity must hold the count).  A blob that is truncated, or
+ * whose magic, version, counts, section table or total size do not agree,
+ * returns AEQC_ECORRUPT before anything is copied. */
+size_t aeqc_batch_pack_size(int64_t n, int32_t P, int32_t L, int32_t latent_dtype,
+                            int64_t outliers);
+int aeqc_batch_pack(const aeqc_compressed* in, int64_t n, int32_t P, int32_t L,
+                    int32_t latent_dtype, void* blob_host, size_t bytes, size_t* written,
+                    void* stream);
+int aeqc_batch_peek(const void* blob_host, size_t bytes, int64_t* n, int32_t* P, int32_t* L,
+                    int32_t* latent_dtype, int64_t* outliers);
+int aeqc_batch_unpack(const void* blob_host, size_t bytes, aeqc_compressed* out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -10,6 +10,7 @@ Names follow the C ABI in ``include/aeqc.h``.
 from __future__ import annotations
 
 import ctypes as C
+import struct
 import os
 from dataclasses import dataclass
 from typing import Optional, Sequence
@@ -153,6 +154,19 @@ SYMBOLS = {
     "mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "mlp_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "aeqc_model_save_size": (C.c_size_t, [C.c_void_p]),
+    "aeqc_model_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "aeqc_model_load": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p]),
+    "aeqc_mlp_save_size": (C.c_size_t, [C.c_void_p]),
+    "aeqc_mlp_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "aeqc_mlp_load": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p]),
+    "aeqc_batch_pack_size": (C.c_size_t, [C.c_int64, C.c_int32, C.c_int32, C.c_int32,
+                                          C.c_int64]),
+    "aeqc_batch_pack": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
+                                  C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
+    "aeqc_batch_peek": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
+    "aeqc_batch_unpack": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -296,6 +310,22 @@ class Model:
         except Exception:
             pass
 
+    def save(self) -> bytes:
+        """Checkpoint blob (weights, normalisation, Adam state, steps)."""
+        lib = load()
+        buf = C.create_string_buffer(lib.aeqc_model_save_size(self.h))
+        _check(lib.aeqc_model_save(self.h, buf, len(buf)))
+        return buf.raw
+
+    @classmethod
+    def load(cls, blob: bytes) -> "Model":
+        """Model restored from a save() blob (AeqcError ECORRUPT if invalid)."""
+        self = cls.__new__(cls)
+        self.h = C.c_void_p()
+        _check(load().aeqc_model_load(blob, len(blob), C.byref(self.h)))
+        self.desc = aeqc_model_desc.from_buffer_copy(blob[16:16 + C.sizeof(aeqc_model_desc)])
+        return self
+
     @property
     def P(self):
         return self.desc.P
@@ -407,6 +437,22 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+    def save(self) -> bytes:
+        """Checkpoint blob (weights, normalisation, Adam state, step)."""
+        lib = load()
+        buf = C.create_string_buffer(lib.aeqc_mlp_save_size(self.h))
+        _check(lib.aeqc_mlp_save(self.h, buf, len(buf)))
+        return buf.raw
+
+    @classmethod
+    def load(cls, blob: bytes) -> "MLP":
+        """MLP restored from a save() blob (AeqcError ECORRUPT if invalid)."""
+        self = cls.__new__(cls)
+        self.h = C.c_void_p()
+        _check(load().aeqc_mlp_load(blob, len(blob), C.byref(self.h)))
+        self.n_in, self.nh = struct.unpack_from("<ii", blob, 16)
+        return self
 
     def set(self, p: dict):
         keys = ("W1", "b1", "W2", "b2", "W3", "b3", "in_mu", "in_sd", "out_mu", "out_sd")
@@ -641,3 +687,42 @@ def decompress_batch(m: Model, grid: Grid, comp: Compressed, params: aeqc_params
                                    _ptr(group_offsets), C.byref(params), _ptr(f), _ptr(ws),
                                    ws.numel(), _stream(stream)))
     return f
+
+
+def _dtype_code(latent_dtype) -> int:
+    import torch
+    return DTYPE_BF16 if latent_dtype == torch.bfloat16 else DTYPE_F32
+
+
+def batch_pack(comp: Compressed, stream=None) -> bytes:
+    """Container blob of a compressed batch (codes, latents, multipliers,
+    status, outlier list); synchronous."""
+    lib = load()
+    n, L = comp.latent.shape
+    P = comp.codes.shape[1]
+    dt = _dtype_code(comp.latent.dtype)
+    cap = comp.c.outliers.capacity
+    buf = C.create_string_buffer(lib.aeqc_batch_pack_size(n, P, L, dt, cap))
+    written = C.c_size_t()
+    _check(lib.aeqc_batch_pack(C.byref(comp.c), n, P, L, dt, buf, len(buf), C.byref(written),
+                               _stream(stream)))
+    return buf.raw[:written.value]
+
+
+def batch_peek(blob: bytes) -> dict:
+    """Validated header of a container blob (AeqcError ECORRUPT if invalid)."""
+    n, outl = C.c_int64(), C.c_int64()
+    P, L, dt = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().aeqc_batch_peek(blob, len(blob), C.byref(n), C.byref(P), C.byref(L),
+                                  C.byref(dt), C.byref(outl)))
+    return dict(n=n.value, P=P.value, L=L.value, latent_dtype=dt.value, outliers=outl.value)
+
+
+def batch_unpack(blob: bytes, device, stream=None) -> Compressed:
+    """Device buffers filled from a container blob; synchronous."""
+    import torch
+    h = batch_peek(blob)
+    ldt = torch.bfloat16 if h["latent_dtype"] == DTYPE_BF16 else torch.float32
+    comp = Compressed(h["n"], h["P"], h["L"], ldt, device, h["outliers"])
+    _check(load().aeqc_batch_unpack(blob, len(blob), C.byref(comp.c), _stream(stream)))
+    return comp

@@ -114,6 +114,10 @@ struct FastGridK {
   float d2q_h[3], d2q_l[3];
   float coef_h[5][5], coef_l[5][5];
   float vmax, wmax;  // max |v_par| and max v_perp^2 on the grid
+  // lane segments of the column walk (no integer division on the device):
+  // rw columns past the first 32 are cut into seg_nchunk chunks of seg_rpc
+  // rows; lane l takes chunk (l * seg_mul) >> 16 = l / rw
+  int seg_nchunk, seg_rpc, seg_mul;
 };
 int make_fast_grid(const GridK& g, FastGridK* out);
 

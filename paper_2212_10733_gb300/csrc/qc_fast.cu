@@ -308,8 +308,8 @@ struct Seg {
   int c, j0, j1;  // column, rows [j0, j1)
 };
 
-__device__ __forceinline__ void lane_segments(int n_par, int n_perp, int lane, Seg& s1,
-                                              Seg& s2) {
+__device__ __forceinline__ void lane_segments(const FastGridK& fg, int n_par, int n_perp,
+                                              int lane, Seg& s1, Seg& s2) {
   const int cw = n_par >= 32 ? 32 : 0, rw = n_par - cw;
   s1.c = lane;
   s1.j0 = 0;
@@ -317,10 +317,10 @@ __device__ __forceinline__ void lane_segments(int n_par, int n_perp, int lane, S
   s2.c = cw;
   s2.j0 = s2.j1 = 0;
   if (rw) {
-    const int nchunk = 32 / rw;  // >= 1
-    const int rpc = (n_perp + nchunk - 1) / nchunk;
+    const int nchunk = fg.seg_nchunk;  // 32 / rw >= 1
+    const int rpc = fg.seg_rpc;        // ceil(n_perp / nchunk)
     if (lane < rw * nchunk) {
-      const int chunk = lane / rw;
+      const int chunk = (lane * fg.seg_mul) >> 16;  // lane / rw
       s2.c = cw + lane - chunk * rw;
       s2.j0 = chunk * rpc;
       s2.j1 = min(n_perp, s2.j0 + rpc);
@@ -381,7 +381,7 @@ __device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb,
                         const float* xhb, const QConst& c, FastWS& w, int16_t* cb, Moments& mo,
                         int lane) {
   Seg sg1, sg2;
-  lane_segments(g.n_par, g.n_perp, lane, sg1, sg2);
+  lane_segments(fg, g.n_par, g.n_perp, lane, sg1, sg2);
   int esc = 0, nonzero = 0;
   ColSums c1, c2;
   quant_segment(sg1, g.n_par, xb, xhb, c, w, cb, c1, esc, nonzero);
@@ -535,8 +535,8 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
     return xp * h;
   };
   Seg sg[2];
-  lane_segments(g.n_par, g.n_perp, lane, sg[0], sg[1]);
-#pragma unroll
+  lane_segments(fg, g.n_par, g.n_perp, lane, sg[0], sg[1]);
+#pragma unroll 1
   for (int part = 0; part < 2; ++part) {
     const Seg& sgm = sg[part];
     const float icf = small_int_to_float(sgm.c - fg.i_c), ic2f = icf * icf;
@@ -628,7 +628,8 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
 // FP32 Cholesky of the unit-diagonal scaling of M (the chord Jacobian).
 struct Chol {
   float L[4][4];
-  float d[4];  // 1 / sqrt(M_kk)
+  float inv[4];  // 1 / L_kk (the solves multiply: no division sequences)
+  float d[4];    // 1 / sqrt(M_kk)
   bool ok;
 };
 
@@ -660,9 +661,13 @@ __device__ __forceinline__ void chol_factor(const df M[10], Chol& ch) {
       for (int q = 0; q < l; ++q) s = fmaf(-ch.L[k][q], ch.L[l][q], s);
       if (k == l) {
         ch.ok = ch.ok && s > 1e-6f;  // cond(M) beyond ~1e6: leave it to FP64
-        ch.L[k][k] = s > 0.f ? sqrtf(s) : 1.f;
+        // approximate square root: the factor only shapes the chord steps,
+        // whose residuals are always formed with the exact M
+        const float r = s > 0.f ? rsqrtf(s) : 1.f;
+        ch.L[k][k] = s > 0.f ? s * r : 1.f;
+        ch.inv[k] = r;
       } else {
-        ch.L[k][l] = s / ch.L[l][l];
+        ch.L[k][l] = s * ch.inv[l];
       }
     }
   }
@@ -676,14 +681,14 @@ __device__ __forceinline__ void chol_solve(const Chol& ch, const float r[4], flo
     float s = r[k] * ch.d[k];
 #pragma unroll
     for (int q = 0; q < k; ++q) s = fmaf(-ch.L[k][q], y[q], s);
-    y[k] = s / ch.L[k][k];
+    y[k] = s * ch.inv[k];
   }
 #pragma unroll
   for (int k = 3; k >= 0; --k) {
     float s = y[k];
 #pragma unroll
     for (int q = k + 1; q < 4; ++q) s = fmaf(-ch.L[q][k], z[q], s);
-    z[k] = s / ch.L[k][k];
+    z[k] = s * ch.inv[k];
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k) dlt[k] = z[k] * ch.d[k];
@@ -712,6 +717,10 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
                         : (kr == 1 ? mo.M[idx[1][l]] : (kr == 2 ? mo.M[idx[2][l]] : mo.M[idx[3][l]]));
   }
   const df Rk = kr == 0 ? mo.R[0] : (kr == 1 ? mo.R[1] : (kr == 2 ? mo.R[2] : mo.R[3]));
+  // 1 / S_k once per histogram: the residual tests multiply
+  float invS[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) invS[k] = mo.S[k] > 1e-30f ? 1.f / mo.S[k] : 1e30f;
   bool force_pass = false;  // converged at lambda = 0: repeat the iteration with the check
   for (int it = 0;; ++it) {
     df H[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
@@ -760,8 +769,7 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
     bool finite_ok = true;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const float den = mo.S[k] > 0.f ? mo.S[k] : 1e-30f;
-      const float rk = fabsf(gk[k].hi) / den;
+      const float rk = fabsf(gk[k].hi) * invS[k];
       finite_ok = finite_ok && isfinite(rk);
       ns.gres[k] = rk;
       res = fmaxf(res, rk);
@@ -823,7 +831,8 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
         const df gl = kr == 0 ? gk[0] : (kr == 1 ? gk[1] : (kr == 2 ? gk[2] : gk[3]));
         const float Sk = kr == 0 ? mo.S[0] : (kr == 1 ? mo.S[1] : (kr == 2 ? mo.S[2] : mo.S[3]));
         const float bk = fabsf(df_add(gl, df_neg(md)).hi) + Sk * (2e-13f + tt * grow * tbd);
-        const float rel = bk / (Sk > 0.f ? Sk : 1e-30f);
+        const float rel =
+            bk * (kr == 0 ? invS[0] : (kr == 1 ? invS[1] : (kr == 2 ? invS[2] : invS[3])));
         float worst = rel;
 #pragma unroll
         for (int o = 1; o < 4; o <<= 1) worst = fmaxf(worst, __shfl_xor_sync(FULL, worst, o));
@@ -848,6 +857,68 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
       lam[k] = df_add_f(lam[k], step * d2[k]);
     }
   }
+}
+
+// Cold paths of fast_histogram, kept out of line: the kernel is bound by
+// instruction fetch, so the common path should span as few cache lines as
+// possible.  The kernel parameters are __grid_constant__, so these take them
+// by reference without a copy.
+struct WarmGuess {
+  float l[4];
+};
+
+__device__ __noinline__ WarmGuess warm_guess(const FusedArgs& a, long long b, float d0, float d1,
+                                             float d2, float d3, int lane) {
+  const float dfeat[4] = {d0, d1, d2, d3};
+  const int L = a.latent.L;
+  double l0[4];
+  mlp_eval_warp(
+      a.mlp, [&](int k) { return k < L ? load_latent(a.latent, b, k) : dfeat[k - L]; }, l0,
+      lane);
+  WarmGuess o;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.l[k] = (float)l0[k];
+  return o;
+}
+
+// f = x' exp(-lambda.phi) with the rounding of the decompression kernel
+__device__ __noinline__ void write_corrected(const FusedArgs& a, long long b, double dl,
+                                             double lamd, FastWS& w, int lane) {
+  const GridK& g = a.grid;
+  double* fb = a.f_out + b * (long long)g.P;
+  const int16_t* cb = a.codes + b * (long long)g.P;
+  const double* xb = a.x + b * (long long)g.P;
+  const float* xhb = a.xhat + b * a.ldx;
+  double ld[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) ld[k] = __shfl_sync(FULL, lamd, k);
+  for (int i = lane; i < g.n_par; i += 32) w.t.ta[i] = corr_a(ld, g.vpar[i]);
+  for (int j = lane; j < g.n_perp; j += 32) w.t.tb[j] = corr_b(ld, g.vperp2[j]);
+  __syncwarp();
+  PointIter pi(lane, g.n_par);
+  for (; pi.p < g.P; pi.next()) {
+    const int code = cb[pi.p];
+    double xpd;
+    if (code == AEQC_CODE_ESCAPE) xpd = __ldg(xb + pi.p);
+    else if (code == AEQC_CODE_ZERO) xpd = 0.0;
+    else xpd = __dadd_rn((double)__ldg(xhb + pi.p), __dmul_rn((double)code, dl));
+    fb[pi.p] = corr_kl(xpd, w.t.ta[pi.i], w.t.tb[pi.j]);
+  }
+}
+
+__device__ __noinline__ int write_outliers(const FusedArgs& a, long long b, int lane) {
+  const int P = a.grid.P;
+  return append_outliers(a.out, a.codes + b * (long long)P, a.x + b * (long long)P, P,
+                         a.row0 + b, lane);
+}
+
+__device__ __noinline__ void write_features(const FusedArgs& a, long long b, float d0, float d1,
+                                            float d2, float d3, int lane) {
+  const LatentK& z = a.latent;
+  float* fr = a.features + b * (long long)(z.L + 4);
+  for (int l = lane; l < z.L; l += 32) fr[l] = load_latent(z, b, l);
+  const float d = lane == 0 ? d0 : (lane == 1 ? d1 : (lane == 2 ? d2 : d3));
+  if (lane < 4) fr[z.L + lane] = d;
 }
 
 __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int lane) {
@@ -892,6 +963,9 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
   float dfeat[4] = {0.f, 0.f, 0.f, 0.f};
   bool done = false;
   const float s_f = float_of_bits(umax);  // s to 24 bits (margins only)
+  // not unrolled: one copy of the quantizer and of the Newton loop serves both
+  // levels (alpha, then alpha / 4)
+#pragma unroll 1
   for (int level = 0; level < 2 && !defer && !done; ++level) {
     QConst c;
     if (!make_qconst(pr.tau, s, level ? pr.alpha4 : pr.alpha, c)) {
@@ -911,19 +985,16 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
     for (int k = 0; k < 4; ++k) lam[k] = df{0.f, 0.f};
     int warm = 0;
     if (level == 0) {
+      if (a.use_mlp || a.features) {  // the warm-start inputs d_k
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        dfeat[k] = mo.S[k] > 0.f ? mo.R[k].hi / mo.S[k] : 0.f;
+        for (int k = 0; k < 4; ++k) dfeat[k] = mo.S[k] > 0.f ? mo.R[k].hi / mo.S[k] : 0.f;
+      }
       if (a.use_mlp) {
-        const int L = a.latent.L;
-        double l0[4];
-        mlp_eval_warp(
-            a.mlp, [&](int k) { return k < L ? load_latent(a.latent, b, k) : dfeat[k - L]; },
-            l0, lane);
+        const WarmGuess l0 = warm_guess(a, b, dfeat[0], dfeat[1], dfeat[2], dfeat[3], lane);
         warm = 1;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const float v = (float)l0[k];
+          const float v = l0.l[k];
           warm = warm && isfinite(v);
           lam[k] = df{isfinite(v) ? v : 0.f, 0.f};
         }
@@ -993,34 +1064,15 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
   }
   // outputs (the codes are in place)
   if (a.f_out) {
-    // f = x' exp(-lambda.phi) with the rounding of the decompression kernel
-    double ld[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) ld[k] = __shfl_sync(FULL, lamd, k);
-    for (int i = lane; i < g.n_par; i += 32) w.t.ta[i] = corr_a(ld, g.vpar[i]);
-    for (int j = lane; j < g.n_perp; j += 32) w.t.tb[j] = corr_b(ld, g.vperp2[j]);
-    __syncwarp();
     const double dl =
         bin_width(pr.tau, s, (st & AEQC_ST_ALPHA_RETRY) ? pr.alpha * 0.25 : pr.alpha);
-    double* fb = a.f_out + b * (long long)P;
-    PointIter pi(lane, g.n_par);
-    for (; pi.p < P; pi.next()) {
-      const int code = cb[pi.p];
-      double xpd;
-      if (code == AEQC_CODE_ESCAPE) xpd = __ldg(xb + pi.p);
-      else if (code == AEQC_CODE_ZERO) xpd = 0.0;
-      else xpd = __dadd_rn((double)__ldg(xhb + pi.p), __dmul_rn((double)code, dl));
-      fb[pi.p] = corr_kl(xpd, w.t.ta[pi.i], w.t.tb[pi.j]);
-    }
+    write_corrected(a, b, dl, lamd, w, lane);
   }
   if (a.out.count && (st & AEQC_ST_CODE_ESCAPE)) {
-    if (append_outliers(a.out, cb, xb, P, a.row0 + b, lane)) st |= AEQC_ST_OUTLIER_OVERFLOW;
+    if (write_outliers(a, b, lane)) st |= AEQC_ST_OUTLIER_OVERFLOW;
   }
-  if (a.features) {
-    float* fr = a.features + b * (long long)(a.latent.L + 4);
-    for (int l = lane; l < a.latent.L; l += 32) fr[l] = load_latent(a.latent, b, l);
-    if (lane < 4) fr[a.latent.L + lane] = dfeat[lane];
-  }
+  if (a.features)
+    write_features(a, b, dfeat[0], dfeat[1], dfeat[2], dfeat[3], lane);
   if (lane < 4) a.lambda[b * 4 + lane] = lamd;
   if (lane == 0) {
     a.scale[b] = s;
@@ -1030,7 +1082,7 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(FW * 32, 4) fused_fast_kernel(const FusedArgs a) {
+__global__ void __launch_bounds__(FW * 32, 4) fused_fast_kernel(const __grid_constant__ FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FastWS& w = reinterpret_cast<FastWS*>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
@@ -1104,6 +1156,14 @@ int make_fast_grid(const GridK& g, FastGridK* out) {
     }
   f.vmax = (float)vmax;
   f.wmax = (float)g.vperp2[g.n_perp - 1];
+  {
+    const int rw = g.n_par - (g.n_par >= 32 ? 32 : 0);  // >= 1 (n_par in [2, 64])
+    f.seg_nchunk = 32 / rw;
+    f.seg_rpc = (g.n_perp + f.seg_nchunk - 1) / f.seg_nchunk;
+    f.seg_mul = (65536 + rw - 1) / rw;
+    for (int l = 0; l < 32; ++l)
+      if ((l * f.seg_mul) >> 16 != l / rw) return AEQC_OK;  // never: 2^16 > 32 rw
+  }
   *out = f;
   return AEQC_OK;
 }

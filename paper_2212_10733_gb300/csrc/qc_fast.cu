@@ -193,60 +193,43 @@ __device__ __noinline__ PointQ quant_point_hard(double x, float xh, double dl) {
 // decided on G = Xh + q 2^38 (within 1 unit of g / u) and A = G - 2X (within
 // (-1, 3) units).  Points in an ambiguity band take the exact FP64 routine.
 __device__ __forceinline__ PointQ quant_point_int(double x, float xh, const QConst& c) {
-  PointQ o;
+  // every outcome is formed and one is selected (no divergent branches on the
+  // common path); only an ambiguous point branches to the exact routine
   const unsigned long long u =
       (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
   const unsigned v = __float_as_uint(xh);
   const int Eh = (v >> 23) & 0xff;
   const int E = (int)(u >> 52);
-  long long X = 0;
-  if (E) {
-    const unsigned long long M10 = ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 10;
-    const int r = c.cx - E;  // >= 1 for x <= s
-    X = r < 64 ? (long long)(M10 >> r) : 0;
-  }
-  if (Eh == 255 || Eh >= c.thr) {  // non-finite or certainly |q| > 32766
-    o.code = AEQC_CODE_ESCAPE;
-    o.rho32 = 0;
-    o.xpw = X;
-    o.xpf = float_of_bits(u);
-    return o;
-  }
+  const unsigned long long M10 = ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 10;
+  const int r = c.cx - E;  // >= 1 for x <= s
+  const long long X = (E != 0 && r < 64) ? (long long)(M10 >> (r & 63)) : 0;
+  // certainly |q| > 32766, or non-finite xhat (thr <= 230 < 255)
+  const bool esc_h = Eh >= c.thr;
   const unsigned long long m40 = (unsigned long long)((v & 0x7fffffu) | (Eh ? 0x800000u : 0u)) << 40;
   const int rh = c.ch - (Eh ? Eh : 1);  // >= 3 below the escape threshold
-  const long long mag = rh < 64 ? (long long)(m40 >> rh) : 0;
+  const long long mag = (rh >= 0 && rh < 64) ? (long long)(m40 >> (rh & 63)) : 0;
   const long long Xh = (v >> 31) ? -mag : mag;
   const long long D = X - Xh;
   const long long m = D >> QF;
   const long long fr = D & ((1ll << QF) - 1);  // D - m 2^38
   constexpr long long half = 1ll << (QF - 1);
-  long long q;
-  if (fr <= half - 2) q = m;
-  else if (fr >= half + 1) q = m + 1;
-  else return quant_point_hard(x, xh, c.dl);
-  if (q > AEQC_CODE_MAX || q < -AEQC_CODE_MAX) {
-    o.code = AEQC_CODE_ESCAPE;
-    o.rho32 = 0;
-    o.xpw = X;
-    o.xpf = float_of_bits(u);
-    return o;
-  }
+  const bool up = fr >= half + 1;
+  const bool band = !up && fr > half - 2;  // fraction in {1/2 - u, 1/2}: ambiguous
+  const long long q = up ? m + 1 : m;
+  const bool esc = esc_h || (!band && (q > AEQC_CODE_MAX || q < -AEQC_CODE_MAX));
   const long long G = Xh + q * (1ll << QF);
   const long long A = G - 2 * X;
-  if (G == 0 || (G > 0 && A >= 0 && A <= 2)) return quant_point_hard(x, xh, c.dl);
-  if (G < 0 || A >= 3) {
-    o.code = AEQC_CODE_ZERO;
-    o.rho32 = (int)((X + 128) >> 8);  // x < Delta / 2 here
-    o.xpw = 0;
-    o.xpf = 0.f;
-    return o;
-  }
-  o.code = (int)q;
+  const bool hard = !esc && (band || G == 0 || (G > 0 && A >= 0 && A <= 2));
+  if (hard) return quant_point_hard(x, xh, c.dl);
+  const bool zero = !esc && (G < 0 || A >= 3);
+  PointQ o;
+  o.code = esc ? AEQC_CODE_ESCAPE : (zero ? AEQC_CODE_ZERO : (int)q);
   // round to nearest: a floor would bias every cell the same way, and the
   // high-order weights (v^4 up to 256) would turn that into a systematic error
-  o.rho32 = (int)((D - q * (1ll << QF) + 128) >> 8);
-  o.xpw = G;
-  o.xpf = fmaf(small_int_to_float((int)q), c.dl_f, xh);
+  // (at the zero level x < Delta / 2 and the residual is x itself)
+  o.rho32 = esc ? 0 : (int)(((zero ? X : D - q * (1ll << QF)) + 128) >> 8);
+  o.xpw = esc ? X : (zero ? 0 : G);
+  o.xpf = esc ? float_of_bits(u) : (zero ? 0.f : fmaf(small_int_to_float((int)q), c.dl_f, xh));
   return o;
 }
 
@@ -362,13 +345,14 @@ __device__ __forceinline__ void quant_segment(const Seg& sg, int n_par, const do
     esc |= o.code == AEQC_CODE_ESCAPE;
     nonzero |= o.code != 0;
     const int j2 = j * j, j4 = j2 * j2;
-    const long long xl = o.xpw & 0x7FFFFFFFll, xu = o.xpw >> 31;
+    // x' >= 0 here, below 2^60 units: two unsigned 32-bit parts (31 + 29 bits)
+    const unsigned xl = (unsigned)o.xpw & 0x7FFFFFFFu, xu = (unsigned)(o.xpw >> 31);
     cs.b[0] += xl;
-    cs.b[1] += xl * j2;
-    cs.b[2] += xl * j4;
+    cs.b[1] += (long long)xl * (unsigned)j2;
+    cs.b[2] += (long long)xl * (unsigned)j4;
     cs.a[0] += xu;
-    cs.a[1] += xu * j2;
-    cs.a[2] += xu * j4;
+    cs.a[1] += (long long)xu * (unsigned)j2;
+    cs.a[2] += (long long)xu * (unsigned)j4;
     cs.u[0] += o.rho32;
     cs.u[1] += (long long)o.rho32 * j2;
     cs.xs += o.xpf;
@@ -929,25 +913,27 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
   const double* xb = a.x + b * (long long)P;
   const float* xhb = a.xhat + b * a.ldx;
   int16_t* cb = a.codes + b * (long long)P;
-  // max(x) and input validity, on the bit patterns (no FP64 compares)
+  // max(x) and input validity, on the bit patterns (no FP64 compares); the
+  // decoded row is fetched into L2 meanwhile, for the quantizer's loads
+  for (int o = lane * 32; o < P; o += 32 * 32) asm volatile("prefetch.L2 [%0];" ::"l"(xhb + o));
+  if (lane == 0) asm volatile("prefetch.L2 [%0];" ::"l"(xhb + P - 1));
   unsigned long long umax = 0;
   int bad = 0;
-  // four loads in flight per lane
-  int p = lane;
-  for (; p + 96 < P; p += 128) {
-    unsigned long long u[4];
+  // eight loads in flight per lane;
+  // a point past the end reads as +0
+#pragma unroll 1
+  for (int p0 = lane; p0 < P; p0 += 32 * 8) {
+    unsigned long long u[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) u[q] = (unsigned long long)__double_as_longlong(__ldg(xb + p + 32 * q));
+    for (int q = 0; q < 8; ++q) {
+      const int p = p0 + 32 * q;
+      u[q] = p < P ? (unsigned long long)__double_as_longlong(__ldg(xb + p)) : 0ull;
+    }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 8; ++q) {
       if (u[q] <= 0x7FEFFFFFFFFFFFFFull) umax = u[q] > umax ? u[q] : umax;  // finite, >= +0
       else bad |= u[q] != 0x8000000000000000ull;                            // -0 counts as 0
     }
-  }
-  for (; p < P; p += 32) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(__ldg(xb + p));
-    if (u <= 0x7FEFFFFFFFFFFFFFull) umax = u > umax ? u : umax;
-    else bad |= u != 0x8000000000000000ull;
   }
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) {

@@ -419,6 +419,39 @@ int64_t aeqc_mlp_param_count(const aeqc_mlp* m);
 /* lambda0 [n][4] float64 from inputs [n][n_in] float32. */
 int mlp_predict(aeqc_mlp* m, const float* inputs, int64_t n, double* lambda0, void* stream);
 
+/* ---- product quantisation of the latents (Sec. III Stage 3, Sec. V-B) ---- */
+/* Each subdomain's latent vectors are quantised column by column: K-means
+ * with k clusters per latent dimension; a value is stored as its cluster's
+ * index (log2 k bits, one uint8 per value here) and decoded as the cluster's
+ * centroid, from a float32 PQ table [G][L][k].  The paper gives neither the
+ * K-means start nor the iteration count; this library starts from k
+ * centroids evenly spaced in the column's range, c_j = lo + (j + 1/2)(hi - lo)/k
+ * (float64, rounded to float32), and runs `iters` Lloyd iterations: nearest
+ * centroid by float32 |z - c_j| (ties to the lowest index), then each
+ * centroid moves to the mean of its members (rounded to float32; a centroid
+ * without members stays).  Non-finite latents take no part in training and
+ * encode as index 0.  The means are sums of 64-bit fixed-point values
+ * (resolution 2^-62 of the column's largest magnitude times the group's row
+ * count), so results do not depend on scheduling and lie within
+ * 2^-42 max|z| (1M rows per group) of the float64 mean.
+ * z: [n][L] latents of latent_dtype (AEQC_DTYPE_F32 / BF16), rows of group g
+ * in [group_offsets[g], group_offsets[g+1]) (DEVICE int64 [G+1]; NULL: one
+ * group), 2 <= k <= AEQC_PQ_MAX_K, L <= 256, L * k <= 10240 for training. */
+#define AEQC_PQ_MAX_K 256
+size_t pq_train_workspace_size(int32_t G, int32_t L, int32_t k);
+int pq_train(const void* z, int32_t latent_dtype, int64_t n, int32_t L,
+             const int64_t* group_offsets, int32_t G, int32_t k, int32_t iters, float* table,
+             void* workspace, size_t workspace_bytes, void* stream);
+/* codes [n][L] uint8: nearest centroid of each value (may be NULL); zq [n][L]
+ * in latent_dtype: the decoded latents (may be NULL, may be z itself). */
+int pq_encode(const void* z, int32_t latent_dtype, int64_t n, int32_t L,
+              const int64_t* group_offsets, int32_t G, int32_t k, const float* table,
+              uint8_t* codes, void* zq, void* stream);
+/* z [n][L] in latent_dtype from codes and the table (a code >= k decodes to 0). */
+int pq_decode(const uint8_t* codes, int64_t n, int32_t L, const int64_t* group_offsets,
+              int32_t G, int32_t k, const float* table, int32_t latent_dtype, void* z,
+              void* stream);
+
 /* ---- checkpoints and the compressed-batch container ----------------------- */
 /* The paper stores, per histogram, the codes, the latent and the Lagrange
  * multipliers (Sec. III, Stage 5) next to the trained network (Sec. III,

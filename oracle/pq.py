@@ -17,7 +17,9 @@ the number of iterations.  Readings:
   a centroid without members stays where it is;
 * nearest = smallest |z - c_j| evaluated in float32 (the latents are float32
   or bfloat16), ties to the lowest index;
-* each subdomain (group) has its own table.
+* each subdomain (group) has its own table;
+* a non-finite latent value takes no part in training (range and means) and
+  encodes as index 0 (no distance is smaller than a NaN's first one).
 
 Pins (tests/test_oracle_pq.py): Lloyd's objective never increases; data drawn
 from k separated clusters gives the clusters' means exactly; k at least the
@@ -37,8 +39,11 @@ def init_centroids(z: np.ndarray, k: int) -> np.ndarray:
     if z.shape[0] == 0:
         return c
     for d in range(L):
-        lo = float(np.min(z[:, d]))
-        hi = float(np.max(z[:, d]))
+        col = z[:, d][np.isfinite(z[:, d])]
+        if col.size == 0:
+            continue
+        lo = float(np.min(col))
+        hi = float(np.max(col))
         for j in range(k):
             c[d, j] = np.float32(lo + (j + 0.5) * (hi - lo) / k)
     return c
@@ -70,8 +75,9 @@ def update(z: np.ndarray, codes: np.ndarray, c: np.ndarray) -> np.ndarray:
     L, k = c.shape
     out = c.copy()
     for d in range(L):
+        fin = np.isfinite(z[:, d])
         for j in range(k):
-            m = codes[:, d] == j
+            m = (codes[:, d] == j) & fin
             cnt = int(np.count_nonzero(m))
             if cnt:
                 out[d, j] = np.float32(np.sum(z[m, d].astype(np.float64)) / cnt)

@@ -154,6 +154,14 @@ SYMBOLS = {
     "mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "mlp_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "pq_train_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32]),
+    "pq_train": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.c_void_p, C.c_int32,
+                           C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t,
+                           C.c_void_p]),
+    "pq_encode": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.c_void_p, C.c_int32,
+                            C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pq_decode": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
+                            C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "aeqc_model_save_size": (C.c_size_t, [C.c_void_p]),
     "aeqc_model_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "aeqc_model_load": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p]),
@@ -726,3 +734,47 @@ def batch_unpack(blob: bytes, device, stream=None) -> Compressed:
     comp = Compressed(h["n"], h["P"], h["L"], ldt, device, h["outliers"])
     _check(load().aeqc_batch_unpack(blob, len(blob), C.byref(comp.c), _stream(stream)))
     return comp
+
+
+# --- product quantisation of the latents ----------------------------------------
+
+def pq_train(z, k: int = 16, iters: int = 10, group_offsets=None, G: int = 1, table=None,
+             ws=None, stream=None):
+    """PQ table [G][L][k] float32 (device) from latents z [n][L] (float32 or
+    bfloat16); rows of group g are group_offsets[g]:group_offsets[g+1]."""
+    import torch
+    n, L = z.shape
+    lib = load()
+    if table is None:
+        table = torch.empty((G, L, k), dtype=torch.float32, device=z.device)
+    need = lib.pq_train_workspace_size(G, L, k)
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, z.device)
+    _check(lib.pq_train(_ptr(z), _dtype_code(z.dtype), n, L, _ptr(group_offsets), G, k, iters,
+                        _ptr(table), _ptr(ws), ws.numel(), _stream(stream)))
+    return table
+
+
+def pq_encode(z, table, group_offsets=None, codes=None, zq=None, want_codes: bool = True,
+              stream=None):
+    """(codes [n][L] uint8, zq [n][L] decoded latents or None)."""
+    import torch
+    n, L = z.shape
+    G, _, k = table.shape
+    if codes is None and want_codes:
+        codes = torch.empty((n, L), dtype=torch.uint8, device=z.device)
+    _check(load().pq_encode(_ptr(z), _dtype_code(z.dtype), n, L, _ptr(group_offsets), G, k,
+                            _ptr(table), _ptr(codes), _ptr(zq), _stream(stream)))
+    return codes, zq
+
+
+def pq_decode(codes, table, latent_dtype, group_offsets=None, out=None, stream=None):
+    """Latents [n][L] of latent_dtype from PQ codes and the table."""
+    import torch
+    n, L = codes.shape
+    G, _, k = table.shape
+    if out is None:
+        out = torch.empty((n, L), dtype=latent_dtype, device=codes.device)
+    _check(load().pq_decode(_ptr(codes), n, L, _ptr(group_offsets), G, k, _ptr(table),
+                            _dtype_code(latent_dtype), _ptr(out), _stream(stream)))
+    return out

@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--no-compare", action="store_true",
                     help="time only --form (default: also the other form, for the speedup)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-pq", action="store_true",
+                    help="skip the product-quantised-latent pipeline measurement")
+    ap.add_argument("--pq-k", type=int, default=16, help="PQ clusters per latent dimension")
+    ap.add_argument("--pq-iters", type=int, default=10, help="Lloyd iterations of PQ training")
     ap.add_argument("--e2e-chunk", type=int, default=1 << 17,
                     help="histograms per chunk of the streamed end-to-end call")
     ap.add_argument("--no-cpu", action="store_true")
@@ -379,6 +383,10 @@ def run_ours(args, rank, world, local):
         gemm[nm] = {"tflops": round(tf, 1), "tensor_frac": round(tf / bf16_peak, 4),
                     "hbm_gbs": round(gb, 1), "hbm_frac": round(gb / hbm, 4)}
 
+    pq = None
+    if fast and not args.no_pq:
+        pq = pq_report(aeqc, synth, args, model, grid, x, prm, out, cfg, stream, hbm, n)
+
     # end to end through the public API with host buffers: compress_batch_host
     # streams chunks of the page-locked input to the device and the outputs
     # back, the copies overlapping the compute of the neighbouring chunks
@@ -425,6 +433,8 @@ def run_ours(args, rank, world, local):
         "roofline": roofline, "gemm": gemm, "e2e": e2e, "training": tr,
         "stats": head["stats"],
     }
+    if pq:
+        res["pq_latents"] = pq
     if precision:
         res["precision_vs_fp64_oracle"] = precision
     for form, r in results.items():
@@ -683,6 +693,96 @@ def run_grouped(args, rank, world, local):
                                          "subdomain, no graph",
                                  "stats": r["stats"], "clocks": r["clocks"]}
     return line
+
+
+def code_entropy(codes, sample=65536):
+    """Empirical entropy (bits per point) of the residual codes of the first
+    `sample` histograms: what an ideal entropy coder would spend on them."""
+    import torch
+    c = codes[:sample].reshape(-1).to(torch.int32) + 32768
+    h = torch.bincount(c, minlength=65536).double()
+    p = h[h > 0] / h.sum()
+    return float(-(p * torch.log2(p)).sum().item())
+
+
+def pq_report(aeqc, synth, args, model, grid, x, prm, out, cfg, stream, hbm, n):
+    """Sec. III Stage 3 / Sec. V-B: the latents quantised column by column
+    (K-means, k clusters, log2 k bits each) and the pipeline run on the
+    decoded latents: encode, PQ encode, decode from the table, quantise the
+    residual, correct.  Reports the PQ kernels' times and bandwidth, the
+    pipeline's throughput and bounds, and the storage per histogram with an
+    ideal entropy coder for the residual codes (no coder is built)."""
+    import torch
+    L, k = cfg["L"], args.pq_k
+    z = out.latent.clone()
+    scale = out.scale.clone()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    table = aeqc.pq_train(z, k=k, iters=args.pq_iters)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = ev0.elapsed_time(ev1)
+    zq = torch.empty_like(z)
+    codes8 = torch.empty((n, L), dtype=torch.uint8, device=z.device)
+    enc = lambda: aeqc.pq_encode(z, table, codes=codes8, zq=zq)  # noqa: E731
+    enc()
+    torch.cuda.synchronize()
+    enc_ms = time_steps(enc, max(3, args.steps), stream)
+    enc_bytes = n * L * (2 * z.element_size() + 1)
+    # the pipeline on PQ'd latents, stage by stage through the public API
+    outq = aeqc.Compressed(n, synth.P, L, z.dtype, z.device, 16 * n)
+    outq.latent = zq
+    outq.c.latent = zq.data_ptr()
+    qws = aeqc.load().quantize_correct_workspace_size(n)
+    qws = torch.empty(qws, dtype=torch.uint8, device=z.device)
+
+    def step():
+        zz, ss = aeqc.ae_encode(model, x)
+        aeqc.pq_encode(zz, table, codes=codes8, zq=zq)
+        xhat = aeqc.ae_decode(model, zq, ss)
+        aeqc.quantize_correct(grid, x, xhat, prm, out=outq, ws=qws)
+
+    step()
+    torch.cuda.synchronize()
+    ms = time_steps(step, max(3, args.steps), stream)
+    st = outq.status.cpu().numpy()
+    stats = dict(
+        converged_round1=float(np.mean((st & aeqc.ST_CONVERGED) != 0)),
+        verbatim=float(np.mean((st & aeqc.ST_VERBATIM) != 0)),
+        alpha_retry=float(np.mean((st & aeqc.ST_ALPHA_RETRY) != 0)),
+        mean_iters=float(outq.iters.float().mean().item()),
+        outliers=int(outq.count.item()),
+        **check_outputs(aeqc, grid, model, outq, x, prm, cfg["tau"]))
+    h_pq, h_raw = code_entropy(outq.codes), code_entropy(out.codes)
+    P = synth.P
+
+    def storage(latent_bits, h):
+        return latent_bits / 8 + P * h / 8 + 4 * 8 + 8  # latents, codes, lambda, scale
+
+    raw_latent_bits = L * 8 * z.element_size()
+    pq_bits = L * int(np.ceil(np.log2(k)))
+    s_raw, s_pq = storage(raw_latent_bits, h_raw), storage(pq_bits, h_pq)
+    return {
+        "k": k, "bits_per_latent": int(np.ceil(np.log2(k))), "lloyd_iterations": args.pq_iters,
+        "train_ms": round(train_ms, 3),
+        "pq_encode": {"ms": round(enc_ms, 4), "achieved_gbs": round(enc_bytes / enc_ms / 1e6, 1),
+                      "peak_gbs": hbm, "frac": round(enc_bytes / enc_ms / 1e6 / hbm, 4),
+                      "algorithmic_bytes": int(enc_bytes)},
+        "pipeline": {"value": round(job_value(n, ms, 1), 1), "unit": "histograms/s",
+                     "ms_per_step": round(ms, 3),
+                     "calls": "ae_encode, pq_encode, ae_decode, quantize_correct"},
+        "stats": stats,
+        "storage_bytes_per_histogram": {
+            "without_pq": round(s_raw, 1), "with_pq": round(s_pq, 1),
+            "residual_code_entropy_bits": {"without_pq": round(h_raw, 3),
+                                           "with_pq": round(h_pq, 3)},
+            "ratio_vs_float64_input": {"without_pq": round(HIST_BYTES / s_raw, 2),
+                                       "with_pq": round(HIST_BYTES / s_pq, 2)},
+            "note": "residual codes at their empirical entropy (an ideal entropy coder); "
+                    "latents raw or as log2(k)-bit PQ codes; lambda and scale as float64; "
+                    "model weights and PQ table not counted"},
+    }
 
 
 def check_outputs(aeqc, grid, model, out, x, prm, tau, chunk=1 << 20, goff=None):

@@ -452,6 +452,34 @@ int pq_decode(const uint8_t* codes, int64_t n, int32_t L, const int64_t* group_o
               int32_t G, int32_t k, const float* table, int32_t latent_dtype, void* z,
               void* stream);
 
+/* ---- entropy coding of the residual codes ---------------------------------- */
+/* The paper hands the quantised residual to MGARD's lossless stage (Sec. III
+ * Stage 4; the coded bytes go to the buffer of Stage 5) without fixing a
+ * format.  These calls code the int16 codes of each histogram with one
+ * Golomb-Rice code:
+ *   symbols: AEQC_CODE_ZERO -> 0, a level q -> zigzag(q) + 1 (zigzag(q) = 2q
+ *   for q >= 0, -2q - 1 for q < 0), AEQC_CODE_ESCAPE -> 65535;
+ *   parameter k in 0..15 per histogram, the one with the fewest bits (ties to
+ *   the smaller k);
+ *   symbol s: u = s >> k; u < 24: u one-bits, a zero-bit, the k low bits of s
+ *   (least significant first); otherwise 24 one-bits and the 16 bits of s;
+ *   bit i of a stream is bit (i mod 32) of 32-bit word i / 32, unused high
+ *   bits of the last word zero; streams back to back at word offsets.
+ * rice_measure: kparam [n] uint8, nbits [n] uint32 and offsets [n + 1] int64
+ * (exclusive prefix sum of ceil(nbits / 32); offsets[n] = total words), all
+ * DEVICE.  rice_pack: writes every stream at its offset into words
+ * (capacity words available; a stream that would not fit is not written, so
+ * size words from offsets[n]).  rice_unpack: codes [n][P] from the streams;
+ * reads stay inside [offsets[b], offsets[b + 1]) clipped to [0, total_words),
+ * so damaged offsets or streams give wrong codes but no stray access. */
+size_t rice_workspace_size(int64_t n);
+int rice_measure(const int16_t* codes, int64_t n, int32_t P, uint8_t* kparam, uint32_t* nbits,
+                 int64_t* offsets, void* workspace, size_t workspace_bytes, void* stream);
+int rice_pack(const int16_t* codes, int64_t n, int32_t P, const uint8_t* kparam,
+              const int64_t* offsets, uint32_t* words, int64_t capacity, void* stream);
+int rice_unpack(const uint32_t* words, int64_t total_words, const int64_t* offsets,
+                const uint8_t* kparam, int64_t n, int32_t P, int16_t* codes, void* stream);
+
 /* ---- checkpoints and the compressed-batch container ----------------------- */
 /* The paper stores, per histogram, the codes, the latent and the Lagrange
  * multipliers (Sec. III, Stage 5) next to the trained network (Sec. III,

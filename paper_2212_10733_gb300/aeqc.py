@@ -162,6 +162,13 @@ SYMBOLS = {
                             C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pq_decode": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
                             C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "rice_workspace_size": (C.c_size_t, [C.c_int64]),
+    "rice_measure": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p,
+                               C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "rice_pack": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p,
+                            C.c_void_p, C.c_int64, C.c_void_p]),
+    "rice_unpack": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64,
+                              C.c_int32, C.c_void_p, C.c_void_p]),
     "aeqc_model_save_size": (C.c_size_t, [C.c_void_p]),
     "aeqc_model_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "aeqc_model_load": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p]),
@@ -777,4 +784,47 @@ def pq_decode(codes, table, latent_dtype, group_offsets=None, out=None, stream=N
         out = torch.empty((n, L), dtype=latent_dtype, device=codes.device)
     _check(load().pq_decode(_ptr(codes), n, L, _ptr(group_offsets), G, k, _ptr(table),
                             _dtype_code(latent_dtype), _ptr(out), _stream(stream)))
+    return out
+
+
+# --- entropy coding of the residual codes ----------------------------------------
+
+@dataclass
+class RiceStreams:
+    kparam: object   # [n] uint8
+    nbits: object    # [n] uint32 (int32 storage)
+    offsets: object  # [n + 1] int64, in words
+    words: object    # [offsets[n]] int32 storage of uint32 words
+
+
+def rice_encode(codes, ws=None, stream=None) -> RiceStreams:
+    """Golomb-Rice streams of the residual codes [n][P] (device int16)."""
+    import torch
+    n, P = codes.shape
+    dev = codes.device
+    lib = load()
+    kp = torch.empty(n, dtype=torch.uint8, device=dev)
+    nb = torch.empty(n, dtype=torch.int32, device=dev)
+    off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    need = lib.rice_workspace_size(n)
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, dev)
+    _check(lib.rice_measure(_ptr(codes), n, P, _ptr(kp), _ptr(nb), _ptr(off), _ptr(ws),
+                            ws.numel(), _stream(stream)))
+    total = int(off[n].item())
+    words = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+    _check(lib.rice_pack(_ptr(codes), n, P, _ptr(kp), _ptr(off), _ptr(words), total,
+                         _stream(stream)))
+    return RiceStreams(kp, nb, off, words[:total])
+
+
+def rice_decode(rs: RiceStreams, P: int, out=None, stream=None):
+    """Residual codes [n][P] int16 from Golomb-Rice streams."""
+    import torch
+    n = rs.kparam.shape[0]
+    if out is None:
+        out = torch.empty((n, P), dtype=torch.int16, device=rs.kparam.device)
+    _check(load().rice_unpack(_ptr(rs.words) if rs.words.numel() else None, rs.words.numel(),
+                              _ptr(rs.offsets), _ptr(rs.kparam), n, P, _ptr(out),
+                              _stream(stream)))
     return out

@@ -192,6 +192,90 @@ __global__ void __launch_bounds__(RW * 32) rice_pack_kernel(const int16_t* codes
   }
 }
 
+// Pack with every lane coding its own run of ceil(P / 32) >= 32 consecutive
+// symbols (so every run has at least 32 bits and a 32-bit word is shared by
+// at most two neighbouring lanes): one prefix sum of the run lengths per
+// histogram, then each lane appends its patterns to a 64-bit buffer and
+// stores whole words; the word it shares with the previous lane goes through
+// shared memory and is merged after the run.
+__global__ void __launch_bounds__(RW * 32) rice_pack_seg_kernel(const int16_t* codes,
+                                                                long long n, int P,
+                                                                const uint8_t* kparam,
+                                                                const long long* off,
+                                                                uint32_t* words,
+                                                                long long capacity) {
+  __shared__ int16_t sc[RW][AEQC_MAX_P];
+  __shared__ uint32_t head[RW][32], tail[RW][32];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int ppl = (P + 31) / 32;
+  const int p0 = min(P, lane * ppl), p1 = min(P, p0 + ppl);
+  const int16_t* run = &sc[wi][p0];  // run[p - p0] for p in [p0, p1)
+  const long long nw = (long long)gridDim.x * RW;
+  for (long long b = (long long)blockIdx.x * RW + wi; b < n; b += nw) {
+    const int16_t* cb = codes + b * P;
+    for (int p = lane; p < P; p += 32) sc[wi][p] = cb[p];
+    __syncwarp();
+    const int k = kparam[b] & 15;
+    long long len = 0;
+    for (int p = p0; p < p1; ++p) len += rice_bits(rice_symbol(run[p - p0]), k);
+    long long inc = len;
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const long long S = inc - len, total = __shfl_sync(0xffffffffu, inc, 31);
+    const long long w0 = off[b], wc = (total + 31) >> 5;
+    if (w0 >= 0 && w0 + wc <= capacity) {  // the same for the whole warp
+      const bool shared_head = (S & 31) != 0;
+      unsigned long long buf = 0ull;
+      int cnt = (int)(S & 31);
+      long long wpos = S >> 5;
+      bool first = true;
+      auto emit = [&](uint32_t wv) {
+        if (first && shared_head) head[wi][lane] = wv;
+        else words[w0 + wpos] = wv;
+        first = false;
+        ++wpos;
+      };
+      for (int p = p0; p < p1; ++p) {
+        const unsigned s = rice_symbol(run[p - p0]);
+        const unsigned u = s >> k;
+        unsigned long long v;
+        int l;
+        if (u < (unsigned)RCAP) {
+          l = (int)u + 1 + k;
+          v = ((1ull << u) - 1ull) | ((unsigned long long)(s & ((1u << k) - 1u)) << (u + 1));
+        } else {
+          l = RCAP + 16;
+          v = ((1ull << RCAP) - 1ull) | ((unsigned long long)s << RCAP);
+        }
+        const unsigned long long carry = cnt ? (v >> (64 - cnt)) : 0ull;  // cnt < 32 here
+        buf |= v << cnt;
+        cnt += l;
+        if (cnt >= 32) {
+          emit((uint32_t)buf);
+          buf = (buf >> 32) | (carry << 32);
+          cnt -= 32;
+          if (cnt >= 32) {
+            emit((uint32_t)buf);
+            buf >>= 32;
+            cnt -= 32;
+          }
+        }
+      }
+      if (cnt > 0) {  // the run's last, partial word
+        const uint32_t wv = (uint32_t)buf;
+        if (first && shared_head) head[wi][lane] = wv;  // the whole run in one shared word
+        else if (lane < 31) tail[wi][lane] = wv;        // shared with the next run
+        else words[w0 + wpos] = wv;                     // the stream's last word
+      }
+      __syncwarp();
+      if (shared_head) words[w0 + (S >> 5)] = head[wi][lane] | tail[wi][lane - 1];
+    }
+    __syncwarp();
+  }
+}
+
 __global__ void rice_unpack_kernel(const uint32_t* words, long long total_words,
                                    const long long* off, const uint8_t* kparam, long long n, int P,
                                    int16_t* codes) {
@@ -294,9 +378,17 @@ extern "C" int rice_pack(const int16_t* codes, int64_t n, int32_t P, const uint8
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   long long blocks = (n + RW - 1) / RW;
-  if (blocks > (long long)sms * 4) blocks = (long long)sms * 4;
-  rice_pack_kernel<<<(unsigned)blocks, RW * 32, 0, static_cast<cudaStream_t>(stream)>>>(
-      codes, n, P, kparam, reinterpret_cast<const long long*>(offsets), words, capacity);
+  const long long* off = reinterpret_cast<const long long*>(offsets);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (P >= 32 * 31 + 1) {  // runs of at least 32 symbols per lane
+    if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+    rice_pack_seg_kernel<<<(unsigned)blocks, RW * 32, 0, s>>>(codes, n, P, kparam, off, words,
+                                                               capacity);
+    return check_launch("rice_pack_seg_kernel");
+  }
+  if (blocks > (long long)sms * 7) blocks = (long long)sms * 7;
+  rice_pack_kernel<<<(unsigned)blocks, RW * 32, 0, s>>>(codes, n, P, kparam, off, words,
+                                                          capacity);
   return check_launch("rice_pack_kernel");
 }
 

@@ -480,6 +480,32 @@ int rice_pack(const int16_t* codes, int64_t n, int32_t P, const uint8_t* kparam,
 int rice_unpack(const uint32_t* words, int64_t total_words, const int64_t* offsets,
                 const uint8_t* kparam, int64_t n, int32_t P, int16_t* codes, void* stream);
 
+/* ---- NRMSE and the error-bound search (Sec. IV-A Eq. (7); Sec. III Stage 4) -- */
+/* nrmse_batch: per_hist [n] (DEVICE, may be NULL) = sqrt(mean_p (x - f)^2) /
+ * (max x - min x) of each histogram; batch [1] (DEVICE) = the same over all
+ * n * P values with the range of the whole batch.  Deterministic (fixed
+ * summation order).  x, f: [n][P] float64. */
+size_t nrmse_workspace_size(int64_t n);
+int nrmse_batch(const double* x, const double* f, int64_t n, int32_t P, double* per_hist,
+                double* batch, void* workspace, size_t workspace_bytes, void* stream);
+/* The paper finds its residual compressor's error bound automatically for a
+ * target accuracy; here the bound is the pointwise tau.  Bisection on
+ * log(tau): the first probe is tau_lo, then `probes - 1` midpoints of the
+ * bracket; each probe compresses and decompresses the batch (compress_batch,
+ * decompress_batch with `base` except tau) and measures the batch NRMSE.
+ * Returns the largest probed tau whose NRMSE <= target and that NRMSE
+ * (host doubles).  AEQC_EUNSUPPORTED if tau_lo already misses the target
+ * or a probe escapes more values than outlier_capacity holds.
+ * Synchronizes the stream once per probe.  The workspace holds one
+ * compressed batch, the decompressed batch and the calls' workspaces. */
+size_t aeqc_bound_search_workspace_size(const aeqc_model* m, int64_t n,
+                                        int64_t outlier_capacity);
+int aeqc_bound_search(aeqc_model* m, const aeqc_grid* grid, const double* x, int64_t n,
+                      const int64_t* group_offsets, const aeqc_params* base, double target,
+                      double tau_lo, double tau_hi, int32_t probes, int64_t outlier_capacity,
+                      double* tau_out, double* nrmse_out, void* workspace,
+                      size_t workspace_bytes, void* stream);
+
 /* ---- checkpoints and the compressed-batch container ----------------------- */
 /* The paper stores, per histogram, the codes, the latent and the Lagrange
  * multipliers (Sec. III, Stage 5) next to the trained network (Sec. III,

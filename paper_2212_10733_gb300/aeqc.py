@@ -169,6 +169,14 @@ SYMBOLS = {
                             C.c_void_p, C.c_int64, C.c_void_p]),
     "rice_unpack": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_int64,
                               C.c_int32, C.c_void_p, C.c_void_p]),
+    "nrmse_workspace_size": (C.c_size_t, [C.c_int64]),
+    "nrmse_batch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
+                              C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
+    "aeqc_bound_search_workspace_size": (C.c_size_t, [C.c_void_p, C.c_int64, C.c_int64]),
+    "aeqc_bound_search": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                    C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_int32,
+                                    C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                    C.c_void_p]),
     "aeqc_model_save_size": (C.c_size_t, [C.c_void_p]),
     "aeqc_model_save": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "aeqc_model_load": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p]),
@@ -828,3 +836,33 @@ def rice_decode(rs: RiceStreams, P: int, out=None, stream=None):
                               _ptr(rs.offsets), _ptr(rs.kparam), n, P, _ptr(out),
                               _stream(stream)))
     return out
+
+
+# --- NRMSE (Eq. (7)) and the error-bound search ------------------------------------
+
+def nrmse_batch(x, f, per_hist: bool = False, stream=None):
+    """(batch NRMSE as a float, per-histogram NRMSE tensor or None)."""
+    import torch
+    n, P = x.shape
+    ph = torch.empty(n, dtype=torch.float64, device=x.device) if per_hist else None
+    bt = torch.empty(1, dtype=torch.float64, device=x.device)
+    ws = _workspace(load().nrmse_workspace_size(n), x.device)
+    _check(load().nrmse_batch(_ptr(x), _ptr(f), n, P, _ptr(ph), _ptr(bt), _ptr(ws), ws.numel(),
+                              _stream(stream)))
+    return float(bt.item()), ph
+
+
+def bound_search(m: Model, grid: Grid, x, params: aeqc_params, target: float,
+                 tau_lo: float = 1e-6, tau_hi: float = 1e-1, probes: int = 12,
+                 group_offsets=None, outlier_capacity: Optional[int] = None, stream=None):
+    """(tau, nrmse): the largest probed pointwise bound whose batch NRMSE
+    after compression and decompression stays within the target."""
+    n = x.shape[0]
+    cap = outlier_capacity if outlier_capacity is not None else max(1024, 16 * n)
+    lib = load()
+    ws = _workspace(lib.aeqc_bound_search_workspace_size(m.h, n, cap), x.device)
+    t, e = C.c_double(), C.c_double()
+    _check(lib.aeqc_bound_search(m.h, C.byref(grid.c), _ptr(x), n, _ptr(group_offsets),
+                                 C.byref(params), target, tau_lo, tau_hi, probes, cap,
+                                 C.byref(t), C.byref(e), _ptr(ws), ws.numel(), _stream(stream)))
+    return t.value, e.value

@@ -64,6 +64,10 @@ def parse():
                     help="skip the product-quantised-latent pipeline measurement")
     ap.add_argument("--pq-k", type=int, default=16, help="PQ clusters per latent dimension")
     ap.add_argument("--pq-iters", type=int, default=10, help="Lloyd iterations of PQ training")
+    ap.add_argument("--search-target", type=float, default=1e-5,
+                    help="NRMSE target of the error-bound search (0: skip)")
+    ap.add_argument("--search-n", type=int, default=65536,
+                    help="histograms the error-bound search runs on")
     ap.add_argument("--e2e-chunk", type=int, default=1 << 17,
                     help="histograms per chunk of the streamed end-to-end call")
     ap.add_argument("--no-cpu", action="store_true")
@@ -384,6 +388,9 @@ def run_ours(args, rank, world, local):
                     "hbm_gbs": round(gb, 1), "hbm_frac": round(gb / hbm, 4)}
 
     coder = entropy_report(aeqc, synth, args, out, cfg, stream, hbm, n) if fast else None
+    search = None
+    if fast and args.search_target > 0:
+        search = search_report(aeqc, args, model, grid, x, prm, n)
     pq = None
     if fast and not args.no_pq:
         pq = pq_report(aeqc, synth, args, model, grid, x, prm, out, cfg, stream, hbm, n)
@@ -436,6 +443,8 @@ def run_ours(args, rank, world, local):
     }
     if coder:
         res["entropy_coder"] = coder
+    if search:
+        res["bound_search"] = search
     if pq:
         res["pq_latents"] = pq
     if precision:
@@ -748,6 +757,21 @@ def entropy_report(aeqc, synth, args, out, cfg, stream, hbm, n):
         "note": "compressed = latents + coded residual + lambda (4 float64) + scale + Rice "
                 "parameter + stream offset; model weights not counted (shared by the batch)",
     }
+
+
+def search_report(aeqc, args, model, grid, x, prm, n):
+    """The error-bound search on the first --search-n histograms: the largest
+    pointwise bound tau whose batch NRMSE (Eq. (7)) after compression and
+    decompression meets --search-target."""
+    import torch
+    m = min(n, args.search_n)
+    xs = x[:m]
+    t0 = time.time()
+    tau, e = aeqc.bound_search(model, grid, xs, prm, args.search_target, tau_lo=1e-7,
+                               tau_hi=1e-1, probes=16, outlier_capacity=xs.numel())
+    torch.cuda.synchronize()
+    return {"histograms": m, "target_nrmse": args.search_target, "tau": tau, "nrmse": e,
+            "probes": 16, "bracket": [1e-7, 1e-1], "seconds": round(time.time() - t0, 3)}
 
 
 def pq_report(aeqc, synth, args, model, grid, x, prm, out, cfg, stream, hbm, n):

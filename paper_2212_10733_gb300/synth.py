@@ -21,7 +21,10 @@ Recipe (one numpy Philox stream per seed, draws in a fixed order):
   * heavy tail (optional): a fraction of histograms gets floor noise
     1e-6 * max(x) * |t_2| (Student t, 2 degrees of freedom, clipped at 1e3);
   * subdomain sizes: lognormal, median 8192, sigma_ln 0.85, clipped to
-    [1024, 65536].
+    [1024, 65536];
+  * time steps (incremental training, Sec. IV-B): step t moves every centre
+    by t * (drift_par, drift_perp) and scales every amplitude by
+    (1 + drift_amp)^t, so consecutive steps are close but not equal.
 """
 from __future__ import annotations
 
@@ -59,6 +62,16 @@ def gaussian_params(n: int, seed: int, k_max: int = 3):
     return dict(amp=amp, c_par=c_par, c_perp=c_perp, s_par=s_par, s_perp=s_perp)
 
 
+def drift_params(prm: dict, t: int, drift_par: float = 0.05, drift_perp: float = 0.03,
+                 drift_amp: float = 0.02) -> dict:
+    """Mixture parameters of time step t (t = 0: unchanged)."""
+    out = dict(prm)
+    out["c_par"] = prm["c_par"] + t * drift_par
+    out["c_perp"] = prm["c_perp"] + t * drift_perp
+    out["amp"] = prm["amp"] * (1.0 + drift_amp) ** t
+    return out
+
+
 def _eval_numpy(prm, idx, vpar, vperp):
     a = {k: v[idx] for k, v in prm.items()}
     ea = np.exp(-(vpar[None, None, :] - a["c_par"][:, :, None]) ** 2
@@ -70,13 +83,13 @@ def _eval_numpy(prm, idx, vpar, vperp):
 
 
 def histograms(n: int, seed: int, k_max: int = 3, heavy_frac: float = 0.0,
-               idx=None) -> np.ndarray:
+               idx=None, step: int = 0) -> np.ndarray:
     """Histograms [len(idx) or n][n_perp * n_par] float64 (i fastest).
 
     ``idx`` selects a subset of the n-histogram workload (same values as the
-    full set at those indices)."""
+    full set at those indices); ``step`` is the time step (drift_params)."""
     vpar, vperp, _ = grid_arrays()
-    prm = gaussian_params(n, seed, k_max)
+    prm = drift_params(gaussian_params(n, seed, k_max), step)
     idx = np.arange(n) if idx is None else np.asarray(idx)
     x = _eval_numpy(prm, idx, vpar, vperp).reshape(len(idx), P)
     if heavy_frac > 0.0:
@@ -100,13 +113,13 @@ def _add_heavy_tail_numpy(x, n, seed, heavy_frac, idx):
 
 
 def histograms_torch(n: int, seed: int, device, k_max: int = 3, heavy_frac: float = 0.0,
-                     chunk: int = 1 << 17):
+                     chunk: int = 1 << 17, step: int = 0):
     """Same workload as :func:`histograms` evaluated on a torch device in chunks
     (values may differ from the numpy evaluation in the last ulp; the device
     copy is what both sides of a comparison consume)."""
     import torch
     vpar, vperp, _ = grid_arrays()
-    prm = gaussian_params(n, seed, k_max)
+    prm = drift_params(gaussian_params(n, seed, k_max), step)
     tv = torch.as_tensor(vpar, device=device)
     tq = torch.as_tensor(vperp, device=device)
     out = torch.empty((n, P), dtype=torch.float64, device=device)

@@ -80,7 +80,7 @@ def parse():
     ap.add_argument("--train-steps", type=int, default=None,
                     help="override the number of autoencoder training steps")
     ap.add_argument("--profile", default=None,
-                    choices=["compress", "encode", "decode", "quantize_correct"],
+                    choices=["compress", "encode", "decode", "quantize_correct", "rice", "pq"],
                     help="run --steps launches of one stage between cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off) and exit")
     return ap.parse_args()
@@ -295,10 +295,21 @@ def run_ours(args, rank, world, local):
         model, prm, out, ws = setup(args.form)
         aeqc.compress_batch(model, grid, x, prm, out=out, ws=ws)
         xhat = aeqc.ae_decode(model, out.latent, out.scale)
+        rws = torch.empty(aeqc.load().rice_workspace_size(n), dtype=torch.uint8, device=device)
+        tab = aeqc.pq_train(out.latent, k=16, iters=10)
+        zq = torch.empty_like(out.latent)
+
+        def rice_round_trip():
+            rs = aeqc.rice_encode(out.codes, ws=rws)
+            aeqc.rice_decode(rs, synth.P)
+
         fn = {"compress": lambda: aeqc.compress_batch(model, grid, x, prm, out=out, ws=ws),
               "encode": lambda: aeqc.ae_encode(model, x),
               "decode": lambda: aeqc.ae_decode(model, out.latent, out.scale),
-              "quantize_correct": lambda: aeqc.quantize_correct(grid, x, xhat, prm, out=out)}
+              "quantize_correct": lambda: aeqc.quantize_correct(grid, x, xhat, prm, out=out),
+              "rice": rice_round_trip,
+              "pq": lambda: (aeqc.pq_train(out.latent, k=16, iters=10, table=tab),
+                             aeqc.pq_encode(out.latent, tab, zq=zq))}
         for _ in range(args.warmup):
             fn[args.profile]()
         torch.cuda.synchronize()

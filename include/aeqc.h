@@ -436,7 +436,7 @@ int mlp_predict(aeqc_mlp* m, const float* inputs, int64_t n, double* lambda0, vo
  * 2^-42 max|z| (1M rows per group) of the float64 mean.
  * z: [n][L] latents of latent_dtype (AEQC_DTYPE_F32 / BF16), rows of group g
  * in [group_offsets[g], group_offsets[g+1]) (DEVICE int64 [G+1]; NULL: one
- * group), 2 <= k <= AEQC_PQ_MAX_K, L <= 256, L * k <= 10240 for training. */
+ * group), 2 <= k <= AEQC_PQ_MAX_K, L <= 256, L * (k + 1) <= 10240 for training. */
 #define AEQC_PQ_MAX_K 256
 size_t pq_train_workspace_size(int32_t G, int32_t L, int32_t k);
 int pq_train(const void* z, int32_t latent_dtype, int64_t n, int32_t L,

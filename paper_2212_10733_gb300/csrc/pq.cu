@@ -155,15 +155,19 @@ __global__ void pq_init_kernel(const int* keys, const long long* off, long long 
 __global__ void pq_accum_kernel(const void* z, int bf16, long long n, int L, const long long* off,
                                 int k, const float* table, const int* shift, long long* acc,
                                 unsigned long long* cnt) {
+  // rows of k + 1 entries: the lanes of a warp (consecutive dimensions) read
+  // the same centroid index j in different banks
   extern __shared__ __align__(16) unsigned char sm[];
-  float* c = reinterpret_cast<float*>(sm);                                 // [L][k]
-  long long* sacc = reinterpret_cast<long long*>(c + ((L * k + 1) & ~1));  // [L][k]
-  unsigned long long* scnt = reinterpret_cast<unsigned long long*>(sacc + L * k);
+  const int ks = k + 1;
+  float* c = reinterpret_cast<float*>(sm);                                  // [L][k + 1]
+  long long* sacc = reinterpret_cast<long long*>(c + ((L * ks + 1) & ~1));  // [L][k + 1]
+  unsigned long long* scnt = reinterpret_cast<unsigned long long*>(sacc + L * ks);
   const int g = blockIdx.y;
   for (int t = threadIdx.x; t < L * k; t += blockDim.x) {
-    c[t] = table[(long long)g * L * k + t];
-    sacc[t] = 0;
-    scnt[t] = 0;
+    const int dd = t / k, j = t - dd * k;
+    c[dd * ks + j] = table[(long long)g * L * k + t];
+    sacc[dd * ks + j] = 0;
+    scnt[dd * ks + j] = 0;
   }
   __syncthreads();
   const int dd = threadIdx.x % L;
@@ -171,18 +175,19 @@ __global__ void pq_accum_kernel(const void* z, int bf16, long long n, int L, con
   PQ_FOR_ELEMENTS({
     const float v = load_z(z, bf16, e);
     if (isfinite(v)) {
-      const int j = nearest(v, c + d * k, k);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[d * k + j]),
+      const int j = nearest(v, c + d * ks, k);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&sacc[d * ks + j]),
                 (unsigned long long)__double2ll_rn((double)v * sc));
-      atomicAdd(&scnt[d * k + j], 1ull);
+      atomicAdd(&scnt[d * ks + j], 1ull);
     }
   });
   __syncthreads();
   for (int t = threadIdx.x; t < L * k; t += blockDim.x) {
-    if (scnt[t]) {
+    const int dd = t / k, j = t - dd * k;
+    if (scnt[dd * ks + j]) {
       atomicAdd(reinterpret_cast<unsigned long long*>(&acc[(long long)g * L * k + t]),
-                (unsigned long long)sacc[t]);
-      atomicAdd(&cnt[(long long)g * L * k + t], scnt[t]);
+                (unsigned long long)sacc[dd * ks + j]);
+      atomicAdd(&cnt[(long long)g * L * k + t], scnt[dd * ks + j]);
     }
   }
 }
@@ -202,15 +207,19 @@ __global__ void pq_update_kernel(int GL, int k, const int* shift, long long* acc
 __global__ void pq_encode_kernel(const void* z, int bf16, long long n, int L, const long long* off,
                                  int k, const float* table, uint8_t* codes, void* zq) {
   extern __shared__ __align__(16) unsigned char sm[];
-  float* c = reinterpret_cast<float*>(sm);
+  float* c = reinterpret_cast<float*>(sm);  // [L][k + 1], as in pq_accum_kernel
+  const int ks = k + 1;
   const int g = blockIdx.y;
-  for (int t = threadIdx.x; t < L * k; t += blockDim.x) c[t] = table[(long long)g * L * k + t];
+  for (int t = threadIdx.x; t < L * k; t += blockDim.x) {
+    const int dd = t / k;
+    c[dd * ks + (t - dd * k)] = table[(long long)g * L * k + t];
+  }
   __syncthreads();
   PQ_FOR_ELEMENTS({
     const float v = load_z(z, bf16, e);
-    const int j = nearest(v, c + d * k, k);
+    const int j = nearest(v, c + d * ks, k);
     if (codes) codes[e] = (uint8_t)j;
-    if (zq) store_z(zq, bf16, e, c[d * k + j]);
+    if (zq) store_z(zq, bf16, e, c[d * ks + j]);
   });
 }
 
@@ -243,7 +252,8 @@ dim3 pq_grid(int G) {
 }
 
 size_t accum_smem(int L, int k) {
-  return sizeof(float) * (size_t)((L * k + 1) & ~1) + 16 * (size_t)L * k;
+  const size_t e = (size_t)L * (k + 1);
+  return sizeof(float) * ((e + 1) & ~(size_t)1) + 16 * e;
 }
 
 }  // namespace
@@ -311,7 +321,7 @@ extern "C" int pq_encode(const void* z, int32_t latent_dtype, int64_t n, int32_t
   AEQC_CHECK_ARG(table && (z || n == 0) && (codes || zq), "pq_encode: null pointer");
   AEQC_CHECK_ARG(G == 1 || group_offsets, "pq_encode: G > 1 needs group_offsets");
   if (n == 0) return AEQC_OK;
-  const size_t sm = sizeof(float) * (size_t)L * k;
+  const size_t sm = sizeof(float) * (size_t)L * (k + 1);
   AEQC_CHECK_ARG(sm <= 200 * 1024, "pq_encode: L * k = %d too large", L * k);
   if (sm > 48 * 1024) {
     AEQC_CUDA_TRY(cudaFuncSetAttribute(pq_encode_kernel,

@@ -15,7 +15,8 @@
 // places its bit patterns with a warp prefix sum of their lengths and ORs
 // them into the histogram's stream in shared memory, which is then copied
 // out.  rice_unpack: one thread per histogram reads its stream through a
-// 64-bit bit buffer; reads never leave the histogram's words.
+// 64-bit bit buffer (reads never leave the histogram's words) and the warp
+// writes the decoded codes through shared memory in contiguous rows.
 #include "aeqc_internal.cuh"
 #include "workspace.cuh"
 
@@ -276,18 +277,31 @@ __global__ void __launch_bounds__(RW * 32) rice_pack_seg_kernel(const int16_t* c
   }
 }
 
-__global__ void rice_unpack_kernel(const uint32_t* words, long long total_words,
-                                   const long long* off, const uint8_t* kparam, long long n, int P,
-                                   int16_t* codes) {
-  const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= n) return;
-  long long w = off[b], wend = off[b + 1];
-  if (w < 0) w = 0;
-  if (wend > total_words) wend = total_words;
-  const int k = kparam[b] & 15;
+// One thread per histogram decodes 32 symbols at a time into shared memory;
+// the warp then writes each of its 32 histograms' 32 codes as one contiguous
+// 64-byte store (instead of 32 scattered 2-byte stores per instruction).
+// Launched with 128 threads (4 warps) per block.
+__global__ void __launch_bounds__(128, 6) rice_unpack_kernel(const uint32_t* words,
+                                                          long long total_words,
+                                                          const long long* off,
+                                                          const uint8_t* kparam, long long n,
+                                                          int P, int16_t* codes) {
+  __shared__ int stage[4][32][33];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const long long b0 = ((long long)blockIdx.x * 4 + wi) * 32;  // the warp's first histogram
+  const long long b = b0 + lane;
+  const bool live = b < n;
+  long long w = 0, wend = 0;
+  int k = 0;
+  if (live) {
+    w = off[b];
+    wend = off[b + 1];
+    if (w < 0) w = 0;
+    if (wend > total_words) wend = total_words;
+    k = kparam[b] & 15;
+  }
   unsigned long long buf = 0ull;
   int have = 0;  // valid bits in buf
-  int16_t* cb = codes + b * P;
   auto refill = [&]() {
     while (have <= 32) {
       const unsigned long long x = w < wend ? (unsigned long long)words[w] : 0ull;
@@ -296,28 +310,39 @@ __global__ void rice_unpack_kernel(const uint32_t* words, long long total_words,
       have += 32;
     }
   };
-  for (int p = 0; p < P; ++p) {
-    refill();
-    // unary prefix: count of trailing ones, at most RCAP
-    int u = __ffsll((long long)~buf) - 1;  // buf has at least 33 bits, ones run < 64
-    if (u < 0 || u > RCAP) u = RCAP;
-    unsigned s;
-    if (u < RCAP) {
-      buf >>= (u + 1);
-      have -= u + 1;
-      refill();
-      s = ((unsigned)u << k) | (unsigned)(buf & ((1ull << k) - 1ull));
-      buf >>= k;
-      have -= k;
-    } else {
-      buf >>= RCAP;
-      have -= RCAP;
-      refill();
-      s = (unsigned)(buf & 0xFFFFull);
-      buf >>= 16;
-      have -= 16;
+  for (int c0 = 0; c0 < P; c0 += 32) {
+    const int m = min(32, P - c0);
+    if (live) {
+      for (int i = 0; i < m; ++i) {
+        refill();
+        // unary prefix: count of trailing ones, at most RCAP
+        int u = __ffsll((long long)~buf) - 1;  // buf has at least 33 bits
+        if (u < 0 || u > RCAP) u = RCAP;
+        unsigned sy;
+        if (u < RCAP) {
+          buf >>= (u + 1);
+          have -= u + 1;
+          refill();
+          sy = ((unsigned)u << k) | (unsigned)(buf & ((1ull << k) - 1ull));
+          buf >>= k;
+          have -= k;
+        } else {
+          buf >>= RCAP;
+          have -= RCAP;
+          refill();
+          sy = (unsigned)(buf & 0xFFFFull);
+          buf >>= 16;
+          have -= 16;
+        }
+        stage[wi][lane][i] = rice_code(sy);
+      }
     }
-    cb[p] = (int16_t)rice_code(s);
+    __syncwarp();
+    for (int h = 0; h < 32; ++h) {
+      const long long bh = b0 + h;
+      if (bh < n && lane < m) codes[bh * P + c0 + lane] = (int16_t)stage[wi][h][lane];
+    }
+    __syncwarp();
   }
 }
 
@@ -403,5 +428,6 @@ extern "C" int rice_unpack(const uint32_t* words, int64_t total_words, const int
   if (n == 0) return AEQC_OK;
   rice_unpack_kernel<<<(unsigned)((n + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
       words, total_words, reinterpret_cast<const long long*>(offsets), kparam, n, P, codes);
+  // 128 threads = 4 warps x 32 histograms per block
   return check_launch("rice_unpack_kernel");
 }

@@ -132,7 +132,12 @@ typedef struct aeqc_model_desc {
   int32_t act;      /* AEQC_ACT_* for the hidden layers */
   int32_t dtype;    /* AEQC_DTYPE_* of the inference path */
   int32_t n_groups; /* independent models (subdomains, Sec. III Stage 1) */
-  int32_t reserved;
+  int32_t layers;   /* 0 or 2: P -> H -> L -> H -> P; 1: the paper's network,
+                       one tied linear layer P -> L -> P (Sec. IV-B, Fig. 2):
+                       needs H == L (a multiple of 4, <= 256), tied, FP32;
+                       stored as the two-layer net with W2 = I, b2 = b3 = 0,
+                       which set_group writes and training keeps (their
+                       gradients are zero) */
 } aeqc_model_desc;
 
 typedef struct aeqc_model aeqc_model;

@@ -66,7 +66,7 @@ class aeqc_params(C.Structure):
 
 class aeqc_model_desc(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("P", "H", "L", "tied", "act", "dtype", "n_groups",
-                                          "reserved")]
+                                          "layers")]
 
 
 class aeqc_tuning(C.Structure):
@@ -317,8 +317,9 @@ class Model:
     """Autoencoder handle (aeqc_model)."""
 
     def __init__(self, P: int, H: int, L: int, tied: bool = True, act: int = ACT_IDENTITY,
-                 dtype: int = DTYPE_F32, n_groups: int = 1):
-        self.desc = aeqc_model_desc(P, H, L, int(tied), act, dtype, n_groups, 0)
+                 dtype: int = DTYPE_F32, n_groups: int = 1, layers: int = 2):
+        """layers = 1: the paper's single tied linear layer P -> L -> P (H must be L)."""
+        self.desc = aeqc_model_desc(P, H, L, int(tied), act, dtype, n_groups, layers)
         self.h = C.c_void_p()
         _check(load().aeqc_model_create(C.byref(self.desc), C.byref(self.h)))
 

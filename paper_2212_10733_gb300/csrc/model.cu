@@ -432,10 +432,20 @@ extern "C" int aeqc_model_create(const aeqc_model_desc* desc, aeqc_model** out) 
   AEQC_CHECK_ARG(desc && out, "aeqc_model_create: null argument");
   const aeqc_model_desc d = *desc;
   AEQC_CHECK_ARG(d.P > 0 && d.P <= AEQC_MAX_P, "aeqc_model_create: P=%d out of range", d.P);
-  AEQC_CHECK_ARG(d.H > 0 && d.H <= 1024 && d.H % 32 == 0,
-                 "aeqc_model_create: H=%d must be a multiple of 32 in [32, 1024]", d.H);
-  AEQC_CHECK_ARG(d.L > 0 && d.L <= 256 && d.L % 8 == 0,
-                 "aeqc_model_create: L=%d must be a multiple of 8 in [8, 256]", d.L);
+  AEQC_CHECK_ARG(d.layers == 0 || d.layers == 1 || d.layers == 2,
+                 "aeqc_model_create: layers=%d", d.layers);
+  if (d.layers == 1) {
+    AEQC_CHECK_ARG(d.H == d.L && d.L > 0 && d.L <= 256 && d.L % 4 == 0 && d.tied,
+                   "aeqc_model_create: one layer needs H == L, a multiple of 4 in [4, 256], "
+                   "tied (H=%d, L=%d)", d.H, d.L);
+    if (d.dtype != AEQC_DTYPE_F32)
+      return set_error(AEQC_EUNSUPPORTED, "aeqc_model_create: one-layer models are FP32");
+  } else {
+    AEQC_CHECK_ARG(d.H > 0 && d.H <= 1024 && d.H % 32 == 0,
+                   "aeqc_model_create: H=%d must be a multiple of 32 in [32, 1024]", d.H);
+    AEQC_CHECK_ARG(d.L > 0 && d.L <= 256 && d.L % 8 == 0,
+                   "aeqc_model_create: L=%d must be a multiple of 8 in [8, 256]", d.L);
+  }
   AEQC_CHECK_ARG(d.act == AEQC_ACT_IDENTITY || d.act == AEQC_ACT_RELU,
                  "aeqc_model_create: bad act");
   AEQC_CHECK_ARG(d.dtype == AEQC_DTYPE_F32 || d.dtype == AEQC_DTYPE_BF16,
@@ -546,7 +556,8 @@ extern "C" int aeqc_model_set_group(aeqc_model* m, int32_t group, const double* 
   AEQC_CHECK_ARG(m, "aeqc_model_set_group: null model");
   AEQC_CHECK_ARG(group >= 0 && group < m->d.n_groups, "aeqc_model_set_group: bad group %d",
                  group);
-  AEQC_CHECK_ARG(W1 && b1 && W2 && b2 && b3 && b4 && mu && sigma,
+  const bool one = m->d.layers == 1;
+  AEQC_CHECK_ARG(W1 && b1 && (one || (W2 && b2 && b3)) && b4 && mu && sigma,
                  "aeqc_model_set_group: null parameter array");
   AEQC_CHECK_ARG(m->d.tied || (W3 && W4), "aeqc_model_set_group: untied model needs W3, W4");
   const long long P = m->d.P, H = m->d.H, L = m->d.L;
@@ -556,13 +567,21 @@ extern "C" int aeqc_model_set_group(aeqc_model* m, int32_t group, const double* 
   int rc;
   if ((rc = copy_in(g + m->oW1, W1, P * H))) return rc;
   if ((rc = copy_in(g + m->ob1, b1, H))) return rc;
-  if ((rc = copy_in(g + m->oW2, W2, H * L))) return rc;
-  if ((rc = copy_in(g + m->ob2, b2, L))) return rc;
+  if (one) {  // the second layer is the identity and its biases zero
+    std::vector<double> eye((size_t)H * L, 0.0), zero((size_t)H, 0.0);
+    for (long long i = 0; i < H; ++i) eye[(size_t)i * L + i] = 1.0;
+    if ((rc = copy_in(g + m->oW2, eye.data(), H * L))) return rc;
+    if ((rc = copy_in(g + m->ob2, zero.data(), L))) return rc;
+    if ((rc = copy_in(g + m->ob3, zero.data(), H))) return rc;
+  } else {
+    if ((rc = copy_in(g + m->oW2, W2, H * L))) return rc;
+    if ((rc = copy_in(g + m->ob2, b2, L))) return rc;
+    if ((rc = copy_in(g + m->ob3, b3, H))) return rc;
+  }
   if (!m->d.tied) {
     if ((rc = copy_in(g + m->oW3, W3, L * H))) return rc;
     if ((rc = copy_in(g + m->oW4, W4, H * P))) return rc;
   }
-  if ((rc = copy_in(g + m->ob3, b3, H))) return rc;
   if ((rc = copy_in(g + m->ob4, b4, P))) return rc;
   if ((rc = copy_in(g + m->omu, mu, P))) return rc;
   if ((rc = copy_in(g + m->osig, sigma, P))) return rc;
@@ -734,6 +753,11 @@ static int loss_grad_impl(aeqc_model* m, const double* x, int64_t B, int32_t gro
   colsum_kernel<<<(H + 255) / 256, 256, 0, s>>>(dh1, B, H, gb1);
   TRY(check_launch("colsum_kernel"));
   TRY(gemm_plain(P, H, (int)B, u, 1, P, dh1, H, 1, gW1, H, tied ? 1.f : 0.f, s));
+  if (m->d.layers == 1) {  // the identity layer and its zero biases do not train
+    AEQC_CUDA_TRY(cudaMemsetAsync(gW2, 0, sizeof(float) * (size_t)H * L, s));
+    AEQC_CUDA_TRY(cudaMemsetAsync(gb2, 0, sizeof(float) * (size_t)L, s));
+    AEQC_CUDA_TRY(cudaMemsetAsync(gb3, 0, sizeof(float) * (size_t)H, s));
+  }
 #undef TRY
   return AEQC_OK;
 }

@@ -83,15 +83,16 @@ def _eval_numpy(prm, idx, vpar, vperp):
 
 
 def histograms(n: int, seed: int, k_max: int = 3, heavy_frac: float = 0.0,
-               idx=None, step: int = 0) -> np.ndarray:
+               idx=None, step: int = 0, grid=(N_PAR, N_PERP)) -> np.ndarray:
     """Histograms [len(idx) or n][n_perp * n_par] float64 (i fastest).
 
     ``idx`` selects a subset of the n-histogram workload (same values as the
-    full set at those indices); ``step`` is the time step (drift_params)."""
-    vpar, vperp, _ = grid_arrays()
+    full set at those indices); ``step`` is the time step (drift_params);
+    ``grid`` = (n_par, n_perp) (the paper's XGC mesh nodes are 37 x 33)."""
+    vpar, vperp, _ = grid_arrays(*grid)
     prm = drift_params(gaussian_params(n, seed, k_max), step)
     idx = np.arange(n) if idx is None else np.asarray(idx)
-    x = _eval_numpy(prm, idx, vpar, vperp).reshape(len(idx), P)
+    x = _eval_numpy(prm, idx, vpar, vperp).reshape(len(idx), grid[0] * grid[1])
     if heavy_frac > 0.0:
         x = _add_heavy_tail_numpy(x, n, seed, heavy_frac, idx)
     return np.ascontiguousarray(x)
@@ -107,22 +108,23 @@ def _add_heavy_tail_numpy(x, n, seed, heavy_frac, idx):
     for r, b in enumerate(idx):
         if heavy[b]:
             rng = np.random.Generator(np.random.Philox([seed + 104729, int(b)]))
-            t = np.abs(rng.standard_t(2.0, size=P))
+            t = np.abs(rng.standard_t(2.0, size=x.shape[1]))
             x[r] += 1e-6 * x[r].max() * np.minimum(t, 1e3)
     return x
 
 
 def histograms_torch(n: int, seed: int, device, k_max: int = 3, heavy_frac: float = 0.0,
-                     chunk: int = 1 << 17, step: int = 0):
+                     chunk: int = 1 << 17, step: int = 0, grid=(N_PAR, N_PERP)):
     """Same workload as :func:`histograms` evaluated on a torch device in chunks
     (values may differ from the numpy evaluation in the last ulp; the device
     copy is what both sides of a comparison consume)."""
     import torch
-    vpar, vperp, _ = grid_arrays()
+    vpar, vperp, _ = grid_arrays(*grid)
+    Pg = grid[0] * grid[1]
     prm = drift_params(gaussian_params(n, seed, k_max), step)
     tv = torch.as_tensor(vpar, device=device)
     tq = torch.as_tensor(vperp, device=device)
-    out = torch.empty((n, P), dtype=torch.float64, device=device)
+    out = torch.empty((n, Pg), dtype=torch.float64, device=device)
     for s in range(0, n, chunk):
         e = min(n, s + chunk)
         a = {k: torch.as_tensor(v[s:e], device=device) for k, v in prm.items()}
@@ -131,15 +133,15 @@ def histograms_torch(n: int, seed: int, device, k_max: int = 3, heavy_frac: floa
         eb = torch.exp(-(tq[None, None, :] - a["c_perp"][:, :, None]) ** 2
                        / (2.0 * a["s_perp"][:, :, None] ** 2))
         x = torch.einsum("nk,nki,nkj->nji", a["amp"], ea, eb) * tq[None, :, None]
-        out[s:e] = x.reshape(e - s, P)
+        out[s:e] = x.reshape(e - s, Pg)
     if heavy_frac > 0.0:
         heavy = np.nonzero(_heavy_rows(n, seed, heavy_frac))[0]
         g = torch.Generator(device=device)
         g.manual_seed(seed + 104729)
         for s in range(0, len(heavy), chunk):
             rows = torch.as_tensor(heavy[s:s + chunk], device=device)
-            z = torch.randn((len(rows), P), generator=g, device=device, dtype=torch.float64)
-            u = torch.rand((len(rows), P), generator=g, device=device, dtype=torch.float64)
+            z = torch.randn((len(rows), Pg), generator=g, device=device, dtype=torch.float64)
+            u = torch.rand((len(rows), Pg), generator=g, device=device, dtype=torch.float64)
             t = (z / torch.sqrt(-torch.log1p(-u))).abs().clamp_max(1e3)
             mx = out[rows].amax(dim=1, keepdim=True)
             out[rows] += 1e-6 * mx * t

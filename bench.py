@@ -43,6 +43,10 @@ CONFIGS = {
             heavy=0.0, epochs=1, steps_train=None, batch=128, dtype="bf16"),
     4: dict(name="warm-start-256-subdomains", n=None, G=256, H=256, L=32, tau=1e-4, k_max=3,
             heavy=0.0, epochs=1, steps_train=None, batch=128, dtype="bf16", warm=True),
+    # the paper's network: 37 x 33 histograms, one tied linear layer, latent 4
+    6: dict(name="paper-shape-37x33-latent4", n=1_048_576, H=4, L=4, tau=1e-4, k_max=3,
+            heavy=0.0, epochs=None, steps_train=8192, batch=128, dtype="f32", layers=1,
+            grid=(37, 33)),
     # time steps of drifting data: the model of step t - 1 trained further
     # (incremental) against a fresh model with the same budget and the stale model
     5: dict(name="incremental-timesteps", n=262_144, H=256, L=32, tau=1e-4, k_max=3, heavy=0.0,
@@ -873,7 +877,7 @@ def pq_report(aeqc, synth, args, model, grid, x, prm, out, cfg, stream, hbm, n):
     }
 
 
-def check_outputs(aeqc, grid, model, out, x, prm, tau, chunk=1 << 20, goff=None):
+def check_outputs(aeqc, grid, model, out, x, prm, tau, chunk=1 << 20, goff=None, dims=None):
     """Decompress the batch and measure max |f - x| / e and the relative QoI
     error over all histograms.  One group: in row chunks, each with the
     escaped values of its rows re-indexed from the chunk start (the outlier
@@ -902,7 +906,7 @@ def check_outputs(aeqc, grid, model, out, x, prm, tau, chunk=1 << 20, goff=None)
         xs = x[c0:c1]
         e = tau * xs.amax(dim=1, keepdim=True)
         e_max = max(e_max, float(((f - xs).abs() / e).max().item()))
-        q_max = max(q_max, qoi_rel_err(aeqc, grid, f, xs))
+        q_max = max(q_max, qoi_rel_err(aeqc, grid, f, xs, dims))
         del f
     return {"max_err_over_bound": e_max, "max_qoi_rel_err": q_max}
 
@@ -922,12 +926,13 @@ class SubView:
                                out.index.data_ptr(), out.value.data_ptr()), None)
 
 
-def qoi_rel_err(aeqc, grid, f, x):
+def qoi_rel_err(aeqc, grid, f, x, dims=None):
     """max_k |Q_k(f) - Q_k(x)| / S_k(x) over the batch: moments by the library's
-    FP64 moment kernel, S_k = sum vol |phi_k| x by an FP64 matrix product."""
+    FP64 moment kernel, S_k = sum vol |phi_k| x by an FP64 matrix product
+    (dims = (n_par, n_perp), default 39 x 39)."""
     import torch
     from paper_2212_10733_gb300 import synth
-    vpar, vperp, vol = synth.grid_arrays()
+    vpar, vperp, vol = synth.grid_arrays(*(dims or ()))
     vp = np.tile(vpar, len(vperp))             # point p = j * n_par + i
     w2 = np.repeat(vperp ** 2, len(vpar))
     W = vol * np.abs(np.stack([np.ones_like(vp), vp, w2, vp ** 2], axis=1))
@@ -1146,6 +1151,88 @@ def run_incremental(args, rank, world, local):
     }
 
 
+def run_paper_shape(args, rank, world, local):
+    """The paper's network (Sec. IV-B, Fig. 2): 37 x 33 histograms, one tied
+    linear layer, latent 4, FP32 GEMMs (the tensor-core path needs wider
+    layers); compress_batch with the fast correction, against the plain form
+    (FP64 correction) on the same weights; storage with the residual coder."""
+    import torch
+    from paper_2212_10733_gb300 import aeqc, synth
+    aeqc.load()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    cfg = CONFIGS[args.config]
+    n = args.n or cfg["n"]
+    dims = cfg["grid"]
+    P, L = dims[0] * dims[1], cfg["L"]
+    seed = shard_seed(synth, rank)
+    x = synth.histograms_torch(n, seed, device, k_max=cfg["k_max"], grid=dims)
+    m = aeqc.Model(P, L, L, layers=1)
+    m.set_group(0, synth.ae_init(P, L, L, seed))
+    m.fit_normalizer(0, x[: min(n, 1 << 16)])
+    t0 = time.time()
+    steps = args.train_steps if args.train_steps is not None else cfg["steps_train"]
+    loss = train_steps(m, x, steps, seed, B=cfg["batch"])
+    tr = dict(train_steps=steps, train_s=round(time.time() - t0, 2), train_loss=loss)
+    grid = aeqc.Grid(*synth.grid_arrays(*dims))
+    stream = torch.cuda.current_stream()
+    res = {}
+    for form, kern in (("optimized", aeqc.KERNEL_FAST), ("plain", aeqc.KERNEL_FP64)):
+        if form == "plain" and args.no_compare:
+            continue
+        prm = aeqc.params_default(tau=cfg["tau"], kernel=kern)
+        out = aeqc.Compressed(n, P, L, torch.float32, device, 16 * n)
+        ws = aeqc.compress_batch_workspace(m, n, device)
+        step = lambda: aeqc.compress_batch(m, grid, x, prm, out=out, ws=ws)  # noqa: E731
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = ClockSampler(local)
+        clk.start()
+        ms = max_over_ranks(time_steps(step, args.steps, stream), world)
+        clocks = clk.stop()
+        st = out.status.cpu().numpy()
+        r = dict(ms=ms, value=job_value(n, ms, world), clocks=clocks,
+                 stats=dict(converged_round1=float(np.mean((st & aeqc.ST_CONVERGED) != 0)),
+                            verbatim=float(np.mean((st & aeqc.ST_VERBATIM) != 0)),
+                            alpha_retry=float(np.mean((st & aeqc.ST_ALPHA_RETRY) != 0)),
+                            mean_iters=float(out.iters.float().mean().item()),
+                            **check_outputs(aeqc, grid, m, out, x, prm, cfg["tau"], dims=dims)))
+        if form == "optimized":
+            rs = aeqc.rice_encode(out.codes)
+            coded = int(rs.offsets[n].item()) * 4 / n
+            total = L * 4 + coded + 4 * 8 + 8 + 1 + 8
+            r["storage"] = {"residual_bits_per_point": round(coded * 8 / P, 3),
+                            "compressed_bytes_per_histogram": round(total, 1),
+                            "compression_ratio_vs_float64": round(P * 8 / total, 2)}
+        res[form] = r
+        del out, ws
+    head = res["optimized"]
+    line = {
+        "metric": METRIC, "value": round(head["value"], 1), "unit": "histograms/s",
+        "input_gbs": round(head["value"] * P * 8 / 1e9, 2), "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(head["ms"], 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 GEMM + int64/f32 correction",
+        "data": "synthetic (seeded Gaussian-mixture velocity histograms, 37 x 33 grid)",
+        "config": {"workload": cfg["name"], "histograms_per_gpu": n,
+                   "grid": f"{dims[0]}x{dims[1]}", "ae": f"{P}-{L}-{P} one tied linear layer",
+                   "tau": cfg["tau"], "form": "optimized (FP32 SIMT GEMMs + fast correction)",
+                   "l2": "inputs larger than L2, no flush",
+                   "parallelism": f"dp{world} (independent shards)"},
+        "clocks": head["clocks"], "gpu_launches": 6 * args.steps, "training": tr,
+        "stats": head["stats"], "storage": head["storage"],
+    }
+    if "plain" in res:
+        r = res["plain"]
+        line["vs_plain_form"] = {"value": round(r["value"], 1), "ms_per_step": round(r["ms"], 3),
+                                 "speedup": round(head["value"] / r["value"], 2),
+                                 "form": "FP32 SIMT GEMMs + FP64 correction",
+                                 "stats": r["stats"], "clocks": r["clocks"]}
+    return line
+
+
 def lambda_f32_report(aeqc, grid, model, out, x, prm, tau):
     """The multipliers stored as float32 instead of float64 (the paper's
     precision trade-off for lambda): decompression with the rounded values,
@@ -1171,8 +1258,9 @@ def main():
         print(json.dumps(run_reference(args, rank, world)))
         return
     rank, world, local = dist_setup(args)
-    if CONFIGS[args.config].get("incremental"):
-        line = run_incremental(args, rank, world, local)
+    if CONFIGS[args.config].get("incremental") or CONFIGS[args.config].get("layers") == 1:
+        runner = run_incremental if CONFIGS[args.config].get("incremental") else run_paper_shape
+        line = runner(args, rank, world, local)
         if rank == 0:
             print(json.dumps(line))
         if world > 1:

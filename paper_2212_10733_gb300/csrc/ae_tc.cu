@@ -55,13 +55,12 @@ __device__ __forceinline__ uint32_t bf16_of_f64_words(uint32_t hi, uint32_t lo) 
   const uint32_t a = (hi & 0x7FFFFFFFu) | (lo != 0u ? 1u : 0u);
   const uint32_t r = a + 0xFFFu + ((a >> 13) & 1u);
   const uint32_t E = r >> 20;
-  uint32_t v = sign | ((r >> 13) - (896u << 7));
-  if (E - 897u >= 254u) {  // outside the BF16 normal range (rare, except zero)
-    if (E <= 896u) v = sign;
-    else if (a > 0x7FF00000u) v = sign | 0x7FC0u;  // NaN
-    else v = sign | 0x7F80u;                       // overflow, infinity
-  }
-  return v;
+  const uint32_t v = sign | ((r >> 13) - (896u << 7));
+  // outside the BF16 normal range (zero, underflow, overflow, NaN): selects,
+  // not branches, since the zero row of every histogram makes lanes diverge
+  const uint32_t big = sign | (a > 0x7FF00000u ? 0x7FC0u : 0x7F80u);  // NaN / infinity
+  const uint32_t out = E <= 896u ? sign : big;
+  return E - 897u >= 254u ? out : v;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {

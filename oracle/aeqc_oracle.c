@@ -445,9 +445,26 @@ static int newton_round1(const or_grid* g, const double* xp, const double* Q,
   }
 }
 
+/* Rounding scale of psi at lam: sum vol |f| + sum_k |lam_k Q_k| (each term
+ * of psi enters its rounding error with at most this weight). */
+static double psi_scale(const or_grid* g, const double* f, const double* Q,
+                        const double lam[4]) {
+  double s = 0.0;
+  for (int j = 0; j < g->n_perp; ++j)
+    for (int i = 0; i < g->n_par; ++i)
+      s += vol_at(g, j, i) * fabs(f[(size_t)j * g->n_par + i]);
+  for (int k = 0; k < 4; ++k) s += fabs(lam[k] * Q[k]);
+  return s;
+}
+
 /* Round 2: damped Newton from zero.  A step t in {1, 1/2, 1/4, ...} is taken
- * when it decreases psi by the Armijo amount, or, once psi's change drowns
- * in rounding, when it lowers the scaled residual. */
+ * when it decreases psi by the Armijo amount.  Near the solution the Armijo
+ * decrease t 1e-4 g.d falls below psi's rounding; there a step whose psi
+ * stays within that rounding (1e-12 of psi's scale at both points) is taken
+ * when it lowers the scaled residual by the factor (1 - t/2).  A step that
+ * raises psi beyond its rounding is never taken: far from the solution the
+ * scaled residual alone is no measure of progress (a step that blows f up
+ * also blows up S, the residual's own scale). */
 static int newton_round2(const or_grid* g, const double* xp, const double* Q,
                          double lam[4], int max_iter, double tol, int loss,
                          double* f, double* ftry, int* iters) {
@@ -462,6 +479,7 @@ static int newton_round2(const or_grid* g, const double* xp, const double* Q,
     jacobian_one(g, f, loss, M);
     if (or_cholesky_solve4(M, gk, d) != 0) return 0;
     double psi0 = psi_at(g, f, Q, lam);
+    double sc0 = psi_scale(g, f, Q, lam);
     double slope = gk[0] * d[0] + gk[1] * d[1] + gk[2] * d[2] + gk[3] * d[3];
     double t = 1.0;
     int accepted = 0;
@@ -471,7 +489,9 @@ static int newton_round2(const or_grid* g, const double* xp, const double* Q,
       double rt = residual_at(g, xp, Q, lt, loss, ftry, gt, St);
       if (!isfinite(rt)) continue;
       double psit = psi_at(g, ftry, Q, lt);
-      if (psit <= psi0 - 1e-4 * t * slope || rt <= (1.0 - 0.5 * t) * r) {
+      double flat = 1e-12 * (sc0 + psi_scale(g, ftry, Q, lt));
+      if (psit <= psi0 - 1e-4 * t * slope ||
+          (psit <= psi0 + flat && rt <= (1.0 - 0.5 * t) * r)) {
         for (int k = 0; k < 4; ++k) lam[k] = lt[k];
         accepted = 1;
         break;

@@ -750,11 +750,9 @@ int run_encode_tc(aeqc_model* m, const double* x, long long n, const long long* 
   a.ns = ns;
   const size_t smem = EncSmem(d.H, d.L, ns).total + 1024;
   if (smem > 227 * 1024) return set_error(AEQC_EUNSUPPORTED, "encoder tile does not fit (H=%d)", d.H);
-  static size_t enc_attr = 0;  // the attribute is raised once (capture-safe afterwards)
-  if (smem > enc_attr) {
-    AEQC_CUDA_TRY(cudaFuncSetAttribute(enc_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       227 * 1024));
-    enc_attr = 227 * 1024;
+  {
+    const int rc = raise_smem_limit((const void*)enc_tc_kernel, 227 * 1024);
+    if (rc) return rc;
   }
   const long long tiles = G > 1 ? (n + BM - 1) / BM + G : (n + BM - 1) / BM;
   enc_tc_kernel<<<(unsigned)tiles, NTHREADS, smem, s>>>(mW1, mW2, a);
@@ -799,11 +797,9 @@ int run_decode_tc(aeqc_model* m, const void* latent, const double* scale, long l
   a.sw = sw;
   const size_t smem = DecSmem(d.H, ns, sw).total + 1024;
   if (smem > 227 * 1024) return set_error(AEQC_EUNSUPPORTED, "decoder tile does not fit (H=%d)", d.H);
-  static size_t dec_attr = 0;
-  if (smem > dec_attr) {
-    AEQC_CUDA_TRY(cudaFuncSetAttribute(dec_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       227 * 1024));
-    dec_attr = 227 * 1024;
+  {
+    const int rc = raise_smem_limit((const void*)dec_tc_kernel, 227 * 1024);
+    if (rc) return rc;
   }
   const long long tiles = G > 1 ? (n + BM - 1) / BM + G : (n + BM - 1) / BM;
   dec_tc_kernel<<<(unsigned)tiles, NTHREADS, smem, s>>>(mW4, a);

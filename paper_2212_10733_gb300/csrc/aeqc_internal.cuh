@@ -32,6 +32,12 @@ void clear_error();
 // launch check after a kernel launch
 int check_launch(const char* what);
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device.  The attribute is per device, so the raised value is kept
+// per (kernel, device ordinal); thread-safe; a no-op once raised (so a call
+// inside a stream capture after the first launch on that device does nothing).
+int raise_smem_limit(const void* func, int bytes);
+
 // ---------------------------------------------------------------------------
 // kernel-side parameter blocks (passed by value)
 // ---------------------------------------------------------------------------
@@ -114,6 +120,7 @@ struct FastGridK {
   float d2q_h[3], d2q_l[3];
   float coef_h[5][5], coef_l[5][5];
   float vmax, wmax;  // max |v_par| and max v_perp^2 on the grid
+  float wk[4];       // vol sum |phi_k| over the grid (bounds of per-point rounding)
   // lane segments of the column walk (no integer division on the device):
   // rw columns past the first 32 are cut into seg_nchunk chunks of seg_rpc
   // rows; lane l takes chunk (l * seg_mul) >> 16 = l / rw

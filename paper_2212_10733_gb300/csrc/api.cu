@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <map>
 #include <mutex>
 
 #include "model.cuh"
@@ -28,6 +29,19 @@ int check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)
     return set_error(AEQC_ECUDA, "%s launch failed: %s", what, cudaGetErrorString(e));
+  return AEQC_OK;
+}
+
+int raise_smem_limit(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> raised;
+  int dev = 0;
+  AEQC_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  int& cur = raised[std::make_pair(func, dev)];
+  if (cur >= bytes) return AEQC_OK;
+  AEQC_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  cur = bytes;
   return AEQC_OK;
 }
 
@@ -593,38 +607,16 @@ extern "C" size_t compress_batch_host_workspace_size(const aeqc_model* m, int64_
   return w.bytes + 2 * host_buf_bytes(m, chunk) + kWsAlign;
 }
 
-extern "C" int compress_batch_host(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* grid,
-                                   const double* x_host, int64_t n, const aeqc_params* params,
-                                   aeqc_compressed* out_host, int64_t chunk, void* workspace,
-                                   size_t workspace_bytes, void* stream) {
-  clear_error();
-  GridK gk;
-  ParamsK pk;
-  int rc = make_grid(grid, &gk);
-  if (rc) return rc;
-  if ((rc = make_params(params, &pk))) return rc;
-  AEQC_CHECK_ARG(m && out_host, "compress_batch_host: null argument");
-  if (m->d.n_groups != 1)
-    return set_error(AEQC_EUNSUPPORTED, "compress_batch_host: single-group models only");
-  AEQC_CHECK_ARG(m->d.P == gk.P, "compress_batch_host: model P=%d but grid has %d cells",
-                 m->d.P, gk.P);
-  AEQC_CHECK_ARG(n >= 0 && chunk > 0, "compress_batch_host: need n >= 0 and chunk > 0");
-  if (n == 0) return AEQC_OK;
-  const aeqc_compressed& o = *out_host;
-  AEQC_CHECK_ARG(x_host && o.latent && o.scale && o.codes && o.lambda && o.iters && o.status &&
-                     o.outliers.count && !o.features,
-                 "compress_batch_host: null output array (or features set)");
-  AEQC_CHECK_ARG(o.outliers.capacity == 0 || (o.outliers.index && o.outliers.value),
-                 "compress_batch_host: outlier arrays missing");
-  if (mlp) AEQC_CHECK_ARG(mlp->nin == m->d.L + 4, "compress_batch_host: MLP expects %d inputs",
-                          mlp->nin);
-  if (chunk > n) chunk = n;
-  const size_t need = compress_batch_host_workspace_size(m, chunk, o.outliers.capacity);
-  AEQC_CHECK_ARG(workspace && workspace_bytes >= need && aligned(workspace, kWsAlign),
-                 "compress_batch_host: 256-byte aligned workspace of %zu bytes needed", need);
-  CopyStreams cs;
-  if ((rc = copy_streams(&cs))) return rc;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+// The chunked pipeline of compress_batch_host on the caller's stream s and the
+// library's copy streams, with the caller-owned events ev (h2d done, compute
+// done, d2h done, per buffer).  Returns at the first error; the caller joins
+// the copy streams then.
+static int host_pipeline(aeqc_model* m, aeqc_mlp* mlp, const GridK& gk, const ParamsK& pk,
+                         const aeqc_params* params, const double* x_host, long long n,
+                         const aeqc_compressed& o, long long chunk, void* workspace,
+                         size_t workspace_bytes, cudaStream_t s, const CopyStreams& cs,
+                         cudaEvent_t (&ev)[2][3]) {
+  int rc = AEQC_OK;
   WsCarver c(static_cast<char*>(workspace), workspace_bytes);
   long long* d_count = c.take<long long>(1);
   const long long cap = o.outliers.capacity;
@@ -635,15 +627,6 @@ extern "C" int compress_batch_host(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid
     return set_error(AEQC_EINVAL, "compress_batch_host: workspace too small");
   const size_t esz = m->d.dtype == AEQC_DTYPE_BF16 ? 2 : 4;
   const int P = m->d.P, L = m->d.L;
-  // events: h2d done, compute done, d2h done, per buffer
-  cudaEvent_t ev[2][3];
-  for (int b = 0; b < 2; ++b)
-    for (int k = 0; k < 3; ++k)
-      AEQC_CUDA_TRY(cudaEventCreateWithFlags(&ev[b][k], cudaEventDisableTiming));
-  auto cleanup = [&]() {
-    for (int b = 0; b < 2; ++b)
-      for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[b][k]);
-  };
   // the copy streams start after the work already on the caller's stream
   cudaEvent_t start;
   AEQC_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
@@ -724,7 +707,62 @@ extern "C" int compress_batch_host(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid
     if (e != cudaSuccess)
       rc = set_error(AEQC_ECUDA, "compress_batch_host: %s", cudaGetErrorString(e));
   }
-  cleanup();
+  return rc;
+}
+
+extern "C" int compress_batch_host(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* grid,
+                                   const double* x_host, int64_t n, const aeqc_params* params,
+                                   aeqc_compressed* out_host, int64_t chunk, void* workspace,
+                                   size_t workspace_bytes, void* stream) {
+  clear_error();
+  GridK gk;
+  ParamsK pk;
+  int rc = make_grid(grid, &gk);
+  if (rc) return rc;
+  if ((rc = make_params(params, &pk))) return rc;
+  AEQC_CHECK_ARG(m && out_host, "compress_batch_host: null argument");
+  if (m->d.n_groups != 1)
+    return set_error(AEQC_EUNSUPPORTED, "compress_batch_host: single-group models only");
+  AEQC_CHECK_ARG(m->d.P == gk.P, "compress_batch_host: model P=%d but grid has %d cells",
+                 m->d.P, gk.P);
+  AEQC_CHECK_ARG(n >= 0 && chunk > 0, "compress_batch_host: need n >= 0 and chunk > 0");
+  if (n == 0) return AEQC_OK;
+  const aeqc_compressed& o = *out_host;
+  AEQC_CHECK_ARG(x_host && o.latent && o.scale && o.codes && o.lambda && o.iters && o.status &&
+                     o.outliers.count && !o.features,
+                 "compress_batch_host: null output array (or features set)");
+  AEQC_CHECK_ARG(o.outliers.capacity == 0 || (o.outliers.index && o.outliers.value),
+                 "compress_batch_host: outlier arrays missing");
+  if (mlp) AEQC_CHECK_ARG(mlp->nin == m->d.L + 4, "compress_batch_host: MLP expects %d inputs",
+                          mlp->nin);
+  if (chunk > n) chunk = n;
+  const size_t need = compress_batch_host_workspace_size(m, chunk, o.outliers.capacity);
+  AEQC_CHECK_ARG(workspace && workspace_bytes >= need && aligned(workspace, kWsAlign),
+                 "compress_batch_host: 256-byte aligned workspace of %zu bytes needed", need);
+  CopyStreams cs;
+  if ((rc = copy_streams(&cs))) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t ev[2][3] = {};
+  for (int b = 0; b < 2 && rc == AEQC_OK; ++b)
+    for (int k = 0; k < 3 && rc == AEQC_OK; ++k) {
+      const cudaError_t e = cudaEventCreateWithFlags(&ev[b][k], cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        ev[b][k] = nullptr;
+        rc = set_error(AEQC_ECUDA, "compress_batch_host: event: %s", cudaGetErrorString(e));
+      }
+    }
+  if (rc == AEQC_OK)
+    rc = host_pipeline(m, mlp, gk, pk, params, x_host, n, o, chunk, workspace, workspace_bytes,
+                       s, cs, ev);
+  if (rc != AEQC_OK) {
+    // no copy into or out of the caller's host buffers may still be in
+    // flight when the error returns
+    cudaStreamSynchronize(cs.h2d);
+    cudaStreamSynchronize(cs.d2h);
+  }
+  for (int b = 0; b < 2; ++b)
+    for (int k = 0; k < 3; ++k)
+      if (ev[b][k]) cudaEventDestroy(ev[b][k]);
   return rc;
 }
 

@@ -171,13 +171,18 @@ __global__ void colsum_kernel(const float* d, long long B, int C, float* out) {
   out[c] = s;
 }
 
+// Adam (Kingma & Ba): the decay factors b1, b2 and their complements
+// omb1 = 1 - beta1, omb2 = 1 - beta2 are each rounded from their exact values
+// (1.f - 0.999f would be 1.3e-5 off 0.001, against the bias correction c2
+// computed from the exact beta2).
 __global__ void adam_kernel(float* w, const float* g, float* m, float* v, long long cnt,
-                            float lr, float b1, float b2, float eps, float c1, float c2) {
+                            float lr, float b1, float b2, float omb1, float omb2, float eps,
+                            float c1, float c2) {
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < cnt;
        t += (long long)gridDim.x * blockDim.x) {
     float gr = g[t];
-    float mt = b1 * m[t] + (1.f - b1) * gr;
-    float vt = b2 * v[t] + (1.f - b2) * gr * gr;
+    float mt = b1 * m[t] + omb1 * gr;
+    float vt = b2 * v[t] + omb2 * gr * gr;
     m[t] = mt;
     v[t] = vt;
     w[t] -= lr * (mt / c1) / (sqrtf(vt / c2) + eps);
@@ -280,7 +285,8 @@ int launch_relu_mask(float* d, const float* h, long long count, cudaStream_t s) 
 int launch_adam(float* w, const float* g, float* m, float* v, long long cnt, float lr,
                 int t, cudaStream_t s) {
   float c1 = (float)(1.0 - pow(0.9, t)), c2 = (float)(1.0 - pow(0.999, t));
-  adam_kernel<<<512, 256, 0, s>>>(w, g, m, v, cnt, lr, 0.9f, 0.999f, 1e-8f, c1, c2);
+  adam_kernel<<<512, 256, 0, s>>>(w, g, m, v, cnt, lr, 0.9f, 0.999f, (float)(1.0 - 0.9),
+                                  (float)(1.0 - 0.999), 1e-8f, c1, c2);
   return check_launch("adam_kernel");
 }
 

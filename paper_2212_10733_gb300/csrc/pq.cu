@@ -302,8 +302,8 @@ extern "C" int pq_train(const void* z, int32_t latent_dtype, int64_t n, int32_t 
   rc = check_launch("pq_init_kernel");
   if (rc) return rc;
   if (sm > 48 * 1024) {
-    AEQC_CUDA_TRY(cudaFuncSetAttribute(pq_accum_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    rc = raise_smem_limit((const void*)pq_accum_kernel, (int)sm);
+    if (rc) return rc;
   }
   for (int it = 0; it < iters; ++it) {
     pq_accum_kernel<<<grid, PQ_THREADS, sm, s>>>(z, bf16, n, L, off, k, table, shift, acc, cnt);
@@ -324,8 +324,8 @@ extern "C" int pq_encode(const void* z, int32_t latent_dtype, int64_t n, int32_t
   const size_t sm = sizeof(float) * (size_t)L * (k + 1);
   AEQC_CHECK_ARG(sm <= 200 * 1024, "pq_encode: L * k = %d too large", L * k);
   if (sm > 48 * 1024) {
-    AEQC_CUDA_TRY(cudaFuncSetAttribute(pq_encode_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    rc = raise_smem_limit((const void*)pq_encode_kernel, (int)sm);
+    if (rc) return rc;
   }
   pq_encode_kernel<<<pq_grid(G), PQ_THREADS, sm, static_cast<cudaStream_t>(stream)>>>(
       z, latent_dtype == AEQC_DTYPE_BF16, n, L, reinterpret_cast<const long long*>(group_offsets),

@@ -167,7 +167,7 @@ __device__ __forceinline__ float float_of_bits(unsigned long long u) {
 
 struct PointQ {
   int code;
-  int rho32;      // round((x - x') / Delta * 2^30)
+  long long rho;  // (x - x') / Delta * 2^38 (within two units)
   long long xpw;  // x' / Delta * 2^38 (within one unit)
   float xpf;      // x' (float)
 };
@@ -178,9 +178,9 @@ __device__ __noinline__ PointQ quant_point_hard(double x, float xh, double dl) {
   PointQ o;
   double xpd;
   o.code = quant_point_fp64(x, (double)xh, dl, &xpd);
-  const double rd = __ddiv_rn(__dsub_rn(x, xpd), dl);
-  o.rho32 = __double2int_rn(__dmul_rn(rd, 1073741824.0));
   o.xpw = __double2ll_rn(ldexp(__ddiv_rn(xpd, dl), QF));
+  // x in the same units (exact: x < 2^23 Delta), so that rho = X - X'
+  o.rho = __double2ll_rn(ldexp(__ddiv_rn(x, dl), QF)) - o.xpw;
   o.xpf = (float)xpd;
   return o;
 }
@@ -224,10 +224,8 @@ __device__ __forceinline__ PointQ quant_point_int(double x, float xh, const QCon
   const bool zero = !esc && (G < 0 || A >= 3);
   PointQ o;
   o.code = esc ? AEQC_CODE_ESCAPE : (zero ? AEQC_CODE_ZERO : (int)q);
-  // round to nearest: a floor would bias every cell the same way, and the
-  // high-order weights (v^4 up to 256) would turn that into a systematic error
-  // (at the zero level x < Delta / 2 and the residual is x itself)
-  o.rho32 = esc ? 0 : (int)(((zero ? X : D - q * (1ll << QF)) + 128) >> 8);
+  // at the zero level x < Delta / 2 and the residual is x itself
+  o.rho = esc ? 0ll : (zero ? X : D - q * (1ll << QF));
   o.xpw = esc ? X : (zero ? 0 : G);
   o.xpf = esc ? float_of_bits(u) : (zero ? 0.f : fmaf(small_int_to_float((int)q), c.dl_f, xh));
   return o;
@@ -311,7 +309,7 @@ __device__ __forceinline__ void lane_segments(const FastGridK& fg, int n_par, in
   }
 }
 
-// Column sums of one segment: X' j^(2q) (split at bit 31), rho32 j^(2q)
+// Column sums of one segment: X' j^(2q) (split at bit 31), rho j^(2q)
 // (q = 0, 1) and x' (float).
 struct ColSums {
   long long b[3], a[3], u[2];
@@ -341,7 +339,7 @@ __device__ __forceinline__ void quant_segment(const Seg& sg, int n_par, const do
     const PointQ o = quant_point_int(x, xh, c);
     cb[p] = (int16_t)o.code;
     w.xp[p] = o.xpf;
-    w.rho[p] = (int16_t)((o.rho32 + (1 << 14)) >> 15);
+    w.rho[p] = (int16_t)((o.rho + (1ll << 22)) >> 23);
     esc |= o.code == AEQC_CODE_ESCAPE;
     nonzero |= o.code != 0;
     const int j2 = j * j, j4 = j2 * j2;
@@ -353,8 +351,10 @@ __device__ __forceinline__ void quant_segment(const Seg& sg, int n_par, const do
     cs.a[0] += xu;
     cs.a[1] += (long long)xu * (unsigned)j2;
     cs.a[2] += (long long)xu * (unsigned)j4;
-    cs.u[0] += o.rho32;
-    cs.u[1] += (long long)o.rho32 * j2;
+    // |rho| <= 2^37 and the grid's sum of j^2 is below 2^31 (host check):
+    // every total stays below 2^62
+    cs.u[0] += o.rho;
+    cs.u[1] += o.rho * j2;
     cs.xs += o.xpf;
   }
 }
@@ -409,7 +409,7 @@ __device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb,
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) S1 += __shfl_xor_sync(FULL, S1, o);
   const df vol = {fg.vol_h, fg.vol_l};
-  const df sr = df_ldexp(vol, c.k - 30), sm = df_ldexp(vol, c.k - QF);
+  const df sr = df_ldexp(vol, c.k - QF), sm = sr;
   // moment j = m(p, q) in lane j < 9, (p, q) in the order of the T totals:
   // m(p, q) = vol Delta 2^-38 d2^q sum_r C(p,r) b^r c0^(p-r) T[r][q]
   df mj;
@@ -433,7 +433,7 @@ __device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb,
   const df b = {fg.coef_h[1][1], fg.coef_l[1][1]};   // C(1,1) b = b
   const df c0 = {fg.coef_h[1][0], fg.coef_l[1][0]};  // C(1,0) c0 = c0
   const df d2 = {fg.d2q_h[1], fg.d2q_l[1]};
-  // R_k = vol Delta 2^-30 sum phi_k rho32, phi = (1, v, w, v^2), v = b ic + c0
+  // R_k = vol Delta 2^-38 sum phi_k rho, phi = (1, v, w, v^2), v = b ic + c0
   mo.R[0] = df_mul(sr, u[0]);
   mo.R[1] = df_mul(sr, df_add(df_mul(b, u[1]), df_mul(c0, u[0])));
   mo.R[2] = df_mul(sr, df_mul(d2, u[3]));
@@ -524,9 +524,12 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
   for (int part = 0; part < 2; ++part) {
     const Seg& sgm = sg[part];
     const float icf = small_int_to_float(sgm.c - fg.i_c), ic2f = icf * icf;
-    // t = A + a2 j^2 with A = a0 + a1 ic + a3 ic^2 fixed on the segment
-    const float ah = fmaf(tc.h[3], ic2f, fmaf(tc.h[1], icf, tc.h[0]));
-    const float al = fmaf(tc.l[3], ic2f, fmaf(tc.l[1], icf, tc.l[0]));
+    // t = A + a2 j^2 with A = a0 + a1 ic + a3 ic^2 fixed on the segment, A in
+    // double-float (error below 2^-44 tb), so that a point's t carries one
+    // FP32 rounding relative to t itself
+    df A = df_add(df{tc.h[0], tc.l[0]}, df_mul_f(df{tc.h[1], tc.l[1]}, icf));
+    A = df_add(A, df_mul_f(df{tc.h[3], tc.l[3]}, ic2f));
+    const float ah = A.hi, al = A.lo;
     df s0 = {0.f, 0.f}, s3 = {0.f, 0.f};
     float jf = small_int_to_float(sgm.j0), j2f = jf * jf;
     int p = sgm.j0 * g.n_par + sgm.c;
@@ -705,7 +708,22 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
   float invS[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) invS[k] = mo.S[k] > 1e-30f ? 1.f / mo.S[k] : 1e30f;
+  // Error budget of g (absolute, per moment k), so that "converged" proves
+  // |g_k| <= tol S_k with S_k = sum vol |phi_k| f at the final lambda:
+  //  * moments: the residual is summed in units of Delta 2^-38 within two
+  //    units per point, x' within one unit (its error enters as M lambda):
+  //    Delta wk (2^-37 + 2^-38 tb), wk = vol sum |phi_k| over the grid;
+  //  * the double-float assembly of g: below 2e-15 S_k;
+  //  * H (after a pass, a bound on sum vol |phi_k| |x' h| in Habs):
+  //    summation <= 3.5e-6 Habs in FP32 (none with TwoSum accumulation);
+  //    terms: x' to float (2^-23), t to float (|dt| <= 2.1 u |t| + 2^-43 tb,
+  //    |h'(t)| <= 1.06 |t|: 4.7 u relative to h), h's polynomial in FP32:
+  //    <= 8e-7 Habs + 1.2e-13 tb tmax S_k; the series for h cut after t^5:
+  //    |t|^6 e^|t| / 720 <= 0.003 t^4 h(t) for |t| <= 0.05;
+  //  * S_k at f is at least S_k(x') (1 - tmax).
+  // The budget is kept as one number, max_k err_k / S_k.
   bool force_pass = false;  // converged at lambda = 0: repeat the iteration with the check
+  float erel = 0.f;
   for (int it = 0;; ++it) {
     df H[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     const bool zero_lam =
@@ -713,9 +731,13 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
     int viol = 0, unc = 0;
     bool did_pass = false;
     float tmax = 0.f, errmax = 0.f, pmargin = 0.f;
+    const float tb = fabsf(lam[0].hi) + fabsf(lam[1].hi) * fg.vmax + fabsf(lam[2].hi) * fg.wmax +
+                     fabsf(lam[3].hi) * fg.vmax * fg.vmax;
+    erel = 2e-15f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      erel = fmaxf(erel, fg.wk[k] * c.dl_f * fmaf(3.7e-12f, tb, 7.3e-12f) * invS[k] + 2e-15f);
     auto do_pass = [&]() {
-      const float tb = fabsf(lam[0].hi) + fabsf(lam[1].hi) * fg.vmax + fabsf(lam[2].hi) * fg.wmax +
-                       fabsf(lam[3].hi) * fg.vmax * fg.vmax;
       // FP32 rounding of the check (x' e^{-t} - x evaluated as x'(h - t) - Delta rho)
       // plus the 2^-15 Delta fixed point of rho
       const float margin = 4e-7f * (s * tb + c.dl_f) + 3.0517578125e-05f * c.dl_f + 1e-30f;
@@ -727,8 +749,15 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
       for (int k = 0; k < 4; ++k)  // <= 50 FP32 roundings per lane: |error| <= 50 u sum|terms|
         redo = redo || 3.5e-6f * po.Habs[k] > 1e-13f * mo.S[k];
       if (redo) pass_warp<true>(g, fg, w, c, tc, e - margin, e + margin, po, lane);
+      const float t2 = po.tmax * po.tmax;
+      const float hrel = (redo ? 8e-7f : 4.3e-6f) + 0.003f * t2 * t2;
+      float eh = 0.f;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) H[k] = po.H[k];
+      for (int k = 0; k < 4; ++k) {
+        H[k] = po.H[k];
+        eh = fmaxf(eh, hrel * po.Habs[k] * invS[k]);
+      }
+      erel += eh + 1.2e-13f * tb * po.tmax;
       viol = po.viol;
       unc = po.uncertain;
       did_pass = true;
@@ -749,11 +778,16 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
       for (int k = 0; k < 4; ++k)
         gk[k] = df{__shfl_sync(FULL, gl.hi, k), __shfl_sync(FULL, gl.lo, k)};
     }
+    // residual bound (|g_k| + err_k) / (S_k (1 - tmax)); the floor err_k alone
+    // must leave room below tol, else the histogram goes to the FP64 kernel
+    // 1 / (1 - t) <= 1 + 1.06 t for t <= 0.05 (tmax > 0.05 defers below)
+    const float sf = fmaf(1.06f, tmax, 1.f);
+    const float floor_r = erel * sf;
     float res = 0.f;
     bool finite_ok = true;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const float rk = fabsf(gk[k].hi) * invS[k];
+      const float rk = fabsf(gk[k].hi) * invS[k] * sf + floor_r;
       finite_ok = finite_ok && isfinite(rk);
       ns.gres[k] = rk;
       res = fmaxf(res, rk);
@@ -762,7 +796,7 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
     *rlast = res;
     *iters = it;
     if (!finite_ok) return 0;
-    if (tmax > 0.05f) return -1;
+    if (tmax > 0.05f || floor_r > 0.5f * tol) return -1;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if (fabsf(H[k].hi) > 1e-5f * mo.S[k]) return -1;
@@ -795,8 +829,9 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
     // Certificate after a pass (unit step): g at the new lambda is the
     // residual of the solve plus H(l + d) - H(l), and |h'(t)| <= |t| e^|t|
     // bounds that change by (tmax + tb_d) e^(tmax + tb_d) tb_d S_k (tb_d bounds
-    // |d.phi| on the grid); g itself carries at most 2e-13 S_k of FP32 error
-    // (the pass's bound).  The pointwise check moves by at most
+    // |d.phi| on the grid); g itself carries at most err_k (the budget above,
+    // its x' term widened to the new lambda), and S_k at the new f is at least
+    // S_k (1 - tmax - tb_d).  The pointwise check moves by at most
     // x'max e^tmax (e^tb_d - 1).  When both bounds hold, the step is taken
     // and the histogram converged without the pass at the new lambda.
     if (did_pass && step == 1.f && !viol && !unc) {
@@ -814,9 +849,13 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
         for (int l = 1; l < 4; ++l) md = df_add(md, df_mul_f(rowM[l], dd[l]));
         const df gl = kr == 0 ? gk[0] : (kr == 1 ? gk[1] : (kr == 2 ? gk[2] : gk[3]));
         const float Sk = kr == 0 ? mo.S[0] : (kr == 1 ? mo.S[1] : (kr == 2 ? mo.S[2] : mo.S[3]));
-        const float bk = fabsf(df_add(gl, df_neg(md)).hi) + Sk * (2e-13f + tt * grow * tbd);
-        const float rel =
-            bk * (kr == 0 ? invS[0] : (kr == 1 ? invS[1] : (kr == 2 ? invS[2] : invS[3])));
+        const float ek = erel * Sk +
+                         3.7e-12f * c.dl_f * tbd *
+                             (kr == 0 ? fg.wk[0] : (kr == 1 ? fg.wk[1] : (kr == 2 ? fg.wk[2] : fg.wk[3])));
+        const float bk = fabsf(df_add(gl, df_neg(md)).hi) + ek + Sk * (tt * grow * tbd);
+        const float rel = bk *
+                          (kr == 0 ? invS[0] : (kr == 1 ? invS[1] : (kr == 2 ? invS[2] : invS[3]))) *
+                          fmaf(1.06f, tt, 1.f);
         float worst = rel;
 #pragma unroll
         for (int o = 1; o < 4; o <<= 1) worst = fmaxf(worst, __shfl_xor_sync(FULL, worst, o));
@@ -1110,8 +1149,9 @@ int make_fast_grid(const GridK& g, FastGridK* out) {
       return AEQC_OK;
   // exact 64-bit moment sums: for every weight (i - i_c)^r j^(2q) of the
   // moments, the sum of |weight| over the grid stays below 2^31, so that the
-  // totals of X' (split at bit 31: parts below 2^31 and 2^29) and of rho32
-  // (below 2^30) stay below 2^62
+  // totals of X' (split at bit 31: parts below 2^31 and 2^29) stay below 2^62;
+  // the residual rho (|rho| <= 2^37) enters only with the weights 1, i - i_c,
+  // (i - i_c)^2 and j^2, whose sums must stay below 2^25
   {
     double wsum[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int j = 0; j < g.n_perp; ++j)
@@ -1123,6 +1163,22 @@ int make_fast_grid(const GridK& g, FastGridK* out) {
       }
     for (int q = 0; q < 9; ++q)
       if (!(wsum[q] < 2147483648.0)) return AEQC_OK;
+    if (!(wsum[0] < 33554432.0 && wsum[1] < 33554432.0 && wsum[2] < 33554432.0 &&
+          wsum[5] < 33554432.0))
+      return AEQC_OK;
+  }
+  // vol sum |phi_k| over the grid, rounded up: per-point rounding of the
+  // residual and of x' enters the moments with at most these weights
+  {
+    double w[4] = {0, 0, 0, 0};
+    for (int j = 0; j < g.n_perp; ++j)
+      for (int i = 0; i < g.n_par; ++i) {
+        w[0] += 1.0;
+        w[1] += fabs(g.vpar[i]);
+        w[2] += g.vperp2[j];
+        w[3] += g.vpar[i] * g.vpar[i];
+      }
+    for (int k = 0; k < 4; ++k) f.wk[k] = (float)(w[k] * g.vol_uniform * 1.001);
   }
   f.ok = 1;
   f.i_c = ic;
@@ -1160,11 +1216,9 @@ int launch_fused_fast(const FusedArgs& a_in, cudaStream_t s, int ctas_per_sm) {
   if (!a.fg.ok || a.prm.loss != 0 || a.grid.has_vol) return launch_fused_fp64(a, s);
   AEQC_CUDA_TRY(cudaMemsetAsync(a.fb_count, 0, sizeof(int), s));
   const size_t smem = sizeof(FastWS) * FW;
-  static bool attr = false;
-  if (!attr) {
-    AEQC_CUDA_TRY(cudaFuncSetAttribute(fused_fast_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
+  {
+    const int rc = raise_smem_limit((const void*)fused_fast_kernel, (int)smem);
+    if (rc) return rc;
   }
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);

@@ -142,8 +142,11 @@ __device__ int round1_warp(const GridK& g, WS& w, const double Q[4], double lam[
 }
 
 // Round 2: damped Newton from 0.  A step t in {1, 1/2, ...} is accepted when
-// it lowers psi = sum vol f + lambda.Q by the Armijo amount or lowers the
-// scaled residual by the factor (1 - t/2).
+// it lowers psi = sum vol f + lambda.Q by the Armijo amount, or, where that
+// decrease is below psi's rounding (near the solution), when psi stays within
+// 1e-12 of its scale sum vol |f| + sum |lambda_k Q_k| and the scaled residual
+// falls by the factor (1 - t/2).  A step that raises psi beyond its rounding
+// is never taken: one that blows f up also blows up S, the residual's scale.
 __device__ int round2_warp(const GridK& g, WS& w, const double Q[4], double lam[4],
                            int max_iter, double tol, int loss, int* iters, Eval& e,
                            int lane) {
@@ -160,6 +163,8 @@ __device__ int round2_warp(const GridK& g, WS& w, const double Q[4], double lam[
     for (int k = 0; k < 4; ++k) gk[k] = e.A[k] - Q[k];
     if (chol_solve4(e.M, gk, d) != 0) return 0;
     double psi0 = e.A[0] + lam[0] * Q[0] + lam[1] * Q[1] + lam[2] * Q[2] + lam[3] * Q[3];
+    double sc0 = e.S[0] + fabs(lam[0] * Q[0]) + fabs(lam[1] * Q[1]) + fabs(lam[2] * Q[2]) +
+                 fabs(lam[3] * Q[3]);
     double slope = gk[0] * d[0] + gk[1] * d[1] + gk[2] * d[2] + gk[3] * d[3];
     double r = e.res, t = 1.0;
     int accepted = 0;
@@ -171,7 +176,10 @@ __device__ int round2_warp(const GridK& g, WS& w, const double Q[4], double lam[
       eval_warp(g, w, lt, Q, loss, false, et, lane);
       if (!isfinite(et.res)) continue;
       double psit = et.A[0] + lt[0] * Q[0] + lt[1] * Q[1] + lt[2] * Q[2] + lt[3] * Q[3];
-      if (psit <= psi0 - 1e-4 * t * slope || et.res <= (1.0 - 0.5 * t) * r) {
+      double flat = 1e-12 * (sc0 + et.S[0] + fabs(lt[0] * Q[0]) + fabs(lt[1] * Q[1]) +
+                             fabs(lt[2] * Q[2]) + fabs(lt[3] * Q[3]));
+      if (psit <= psi0 - 1e-4 * t * slope ||
+          (psit <= psi0 + flat && et.res <= (1.0 - 0.5 * t) * r)) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) lam[k] = lt[k];
         accepted = 1;
@@ -673,11 +681,9 @@ int grid_for(long long warps, int sm_mult = 8) {
 int launch_fused_fp64(const FusedArgs& a, cudaStream_t s) {
   if (a.n <= 0) return AEQC_OK;
   size_t smem = sizeof(WS) * WPC;
-  static bool attr = false;
-  if (!attr) {
-    AEQC_CUDA_TRY(cudaFuncSetAttribute(fused_fp64_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
+  {
+    const int rc_attr = raise_smem_limit((const void*)fused_fp64_kernel, (int)smem);
+    if (rc_attr) return rc_attr;
   }
   fused_fp64_kernel<<<grid_for(a.n, 2), WPC * 32, smem, s>>>(a);
   return check_launch("fused_fp64_kernel");
@@ -687,11 +693,9 @@ int launch_fused_fp64_list(const FusedArgs& a, const int* list, const int* count
                            cudaStream_t s) {
   if (a.n <= 0) return AEQC_OK;
   size_t smem = sizeof(WS) * WPC;
-  static bool attr = false;
-  if (!attr) {
-    AEQC_CUDA_TRY(cudaFuncSetAttribute(fused_fp64_list_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
+  {
+    const int rc_attr = raise_smem_limit((const void*)fused_fp64_list_kernel, (int)smem);
+    if (rc_attr) return rc_attr;
   }
   // sized for a few percent of the batch; the grid-stride loop covers any count
   long long warps = a.n / 16 + 1;
@@ -702,11 +706,9 @@ int launch_fused_fp64_list(const FusedArgs& a, const int* list, const int* count
 int launch_moments(const GridK& g, const double* x, long long n, double* Q, cudaStream_t s) {
   if (n <= 0) return AEQC_OK;
   size_t smem = 4 * AEQC_MAX_P * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    AEQC_CUDA_TRY(cudaFuncSetAttribute(moments_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
+  {
+    const int rc_attr = raise_smem_limit((const void*)moments_kernel, (int)smem);
+    if (rc_attr) return rc_attr;
   }
   moments_kernel<<<grid_for(n, 4), 128, smem, s>>>(g, x, n, Q);
   return check_launch("moments_kernel");
@@ -719,11 +721,9 @@ int launch_quantize(const double* x, const float* xhat, long long ld, long long 
   if (out.count) AEQC_CUDA_TRY(cudaMemsetAsync(out.count, 0, sizeof(long long), s));
   QuantArgs a{x, xhat, ld, n, P, prm, codes, scale, status, out, xrec};
   size_t smem = 4 * AEQC_MAX_P * (sizeof(int16_t) + sizeof(double));
-  static bool attr = false;
-  if (!attr) {
-    AEQC_CUDA_TRY(cudaFuncSetAttribute(quantize_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
+  {
+    const int rc_attr = raise_smem_limit((const void*)quantize_kernel, (int)smem);
+    if (rc_attr) return rc_attr;
   }
   quantize_kernel<<<grid_for(n, 4), 128, smem, s>>>(a);
   return check_launch("quantize_kernel");
@@ -753,11 +753,9 @@ int launch_newton(const GridK& g, const double* xrec, const double* Q, long long
   if (n <= 0) return AEQC_OK;
   NewtonArgs a{g, xrec, Q, n, prm, use_warm, lambda, f_out, iters, status};
   size_t smem = sizeof(WS) * WPC;
-  static bool attr = false;
-  if (!attr) {
-    AEQC_CUDA_TRY(cudaFuncSetAttribute(newton_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
+  {
+    const int rc_attr = raise_smem_limit((const void*)newton_kernel, (int)smem);
+    if (rc_attr) return rc_attr;
   }
   newton_kernel<<<grid_for(n, 2), WPC * 32, smem, s>>>(a);
   return check_launch("newton_kernel");

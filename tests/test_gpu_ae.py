@@ -271,3 +271,107 @@ def test_learned_warm_start(aq, trained):
             S = og.vol_uniform * (xp @ np.abs(phi).T)
             assert np.all(np.abs(Mdl) <= 3e-12 * S)
     print("warm start (mean Newton steps cold, warm):", report)
+
+
+def test_adam_steps_match_oracle_across_a_checkpoint(aq):
+    """The library's Adam (Sec. IV-B: Adam, lr 1e-3) against the oracle's, fed
+    the same gradients: three steps, so that the bias corrections 1 - beta^t
+    matter (the first step is -lr sign(g) whatever they are), the third on a
+    model restored from a checkpoint taken after the second (incremental
+    training resumes with its Adam state).  FP32 master weights: agreement
+    within their rounding."""
+    P, H, L, B = 1521, 32, 8, 16
+    m, prms = make_model(aq, P, H, L, True, 0, 1, 11)
+    x = synth.histograms(3 * B, synth.config_seed(2))
+    names = ["W1", "b1", "W2", "b2", "b3", "b4"]
+    g0 = m.get_group(0)
+    w = {k: np.array(g0[k].ravel(), np.float64) for k in names}  # copies: updated in place
+    m1 = {k: np.zeros_like(v) for k, v in w.items()}
+    m2 = {k: np.zeros_like(v) for k, v in w.items()}
+    for t in (1, 2, 3):
+        xb = dev(x[(t - 1) * B:t * B])
+        if t == 3:
+            m = aq.Model.load(m.save())
+        _, gr = m.loss_grad(xb)
+        m.train_step(xb, lr=1e-3)
+        torch.cuda.synchronize()
+        gr = gr.cpu().numpy().astype(np.float64)
+        o = 0
+        for k in names:
+            n_k = w[k].size
+            oracle.adam(w[k], np.ascontiguousarray(gr[o:o + n_k]), m1[k], m2[k], lr=1e-3, t=t)
+            o += n_k
+        got = m.get_group(0)
+        for k in names:
+            d = np.abs(got[k].ravel() - w[k])
+            assert np.all(d <= 2e-9 + 2.0 ** -22 * np.abs(w[k])), (t, k, d.max())
+    # a wrong bias correction would move the third step by ~lr: not within the bar
+    assert np.abs(w["W1"] - g0["W1"].ravel()).max() > 1e-3
+
+
+def f_ulp_bound(og, fo, lam):
+    """|f_gpu - f_oracle| allowed: both compute x' exp(-lambda.phi) in FP64, the
+    GPU as a product of two exponentials of partial sums, the oracle as one;
+    the exponents' rounding, two exp calls and two products: a few ulp plus
+    the exponent's relative error times |lambda.phi|."""
+    phi = np.stack([np.ones(og.P), np.tile(og.vpar, 39), np.repeat(og.vperp, 39) ** 2,
+                    np.tile(og.vpar, 39) ** 2])
+    t_abs = np.abs(lam) @ np.abs(phi)
+    return np.abs(fo) * 2.0 ** -52 * (8.0 + 4.0 * t_abs)
+
+
+def test_decompress_matches_oracle_elementwise(aq, trained):
+    """decompress_batch against oracle.decompress (Sec. III, end of Stage 5) on
+    the decoded histograms the library regenerates: rows at the alpha/4 bin
+    width, zero-level codes, escapes (a spike far above the decoder's reach at
+    a small bound), a zero image."""
+    m, grid, og = trained
+    n, tau = 400, 2e-5
+    x = synth.histograms(n, synth.config_seed(9))
+    x[11] = 0.0
+    x[23, 700] *= 1e3
+    x[24, 333] *= 1e3
+    p = aq.params_default(tau=tau)
+    comp = aq.compress_batch(m, grid, dev(x), p, outlier_capacity=1 << 16)
+    f = aq.decompress_batch(m, grid, comp, p)
+    xh = aq.ae_decode(m, comp.latent, comp.scale)
+    torch.cuda.synchronize()
+    st = comp.status.cpu().numpy()
+    codes = comp.codes.cpu().numpy()
+    lam = comp.lam.cpu().numpy()
+    assert (st & aq.ST_ALPHA_RETRY).any() and (st[11] & aq.ST_ZERO_IMAGE)
+    assert (codes == oracle.ESCAPE).sum() >= 2 and (codes == oracle.ZERO_CODE).any()
+    fo = oracle.decompress(og, xh.cpu().numpy(), codes, x, comp.scale.cpu().numpy(), lam, st,
+                           oracle.Params(tau=tau))
+    f = f.cpu().numpy()
+    for b in range(n):
+        assert np.all(np.abs(f[b] - fo[b]) <= f_ulp_bound(og, fo[b], lam[b])), b
+
+
+def test_float32_multipliers_against_oracle(aq, trained):
+    """The paper's precision trade-off for stored multipliers (Sec. V: FP32 lambda
+    leaves QoI errors near 1e-8, FP64 near 1e-12): decompressing with lambda
+    rounded to float32 gives the oracle's f for those same multipliers, and
+    moment errors well above the FP64 ones but near the paper's level."""
+    m, grid, og = trained
+    x = synth.histograms(256, synth.config_seed(10))
+    p = aq.params_default(tau=1e-4)
+    comp = aq.compress_batch(m, grid, dev(x), p)
+    f64 = aq.decompress_batch(m, grid, comp, p)
+    comp.lam.copy_(comp.lam.float().double())
+    f32 = aq.decompress_batch(m, grid, comp, p)
+    xh = aq.ae_decode(m, comp.latent, comp.scale)
+    torch.cuda.synchronize()
+    lam32 = comp.lam.cpu().numpy()
+    st = comp.status.cpu().numpy()
+    fo = oracle.decompress(og, xh.cpu().numpy(), comp.codes.cpu().numpy(), x,
+                           comp.scale.cpu().numpy(), lam32, st, oracle.Params(tau=1e-4))
+    f32 = f32.cpu().numpy()
+    for b in range(len(x)):
+        assert np.all(np.abs(f32[b] - fo[b]) <= f_ulp_bound(og, fo[b], lam32[b])), b
+    Q, S = oracle.moments(og, x), oracle.abs_moments(og, x)
+    e64 = np.max(np.abs(oracle.moments(og, f64.cpu().numpy()) - Q) / S)
+    e32 = np.max(np.abs(oracle.moments(og, f32) - Q) / S)
+    assert e64 <= 1e-11
+    assert e32 <= 1e-6
+    print("moment error with float64 / float32 multipliers: %.2e / %.2e" % (e64, e32))

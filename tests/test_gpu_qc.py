@@ -130,23 +130,64 @@ def lam_close(a, b):
     return np.all(np.abs(a - b) <= 1e-9 * np.abs(b) + 1e-11)
 
 
+def phi_of(og):
+    vp = np.tile(og.vpar, len(og.vperp))
+    vq = np.repeat(og.vperp, len(og.vpar)) ** 2
+    return np.stack([np.ones_like(vp), vp, vq, vp * vp])
+
+
 def lam_metric_close(a, b, xp, og, slack=3e-12):
     """lambda is unique, but a solver stopping at |g_k| <= tol S_k only fixes it
     to within tol in the metric of M = sum vol phi phi^T x': two correct
-    solvers on different paths differ by |M (a - b)|_k <= 2 tol S_k."""
-    vp = np.tile(og.vpar, len(og.vperp))
-    vq = np.repeat(og.vperp, len(og.vpar)) ** 2
-    phi = np.stack([np.ones_like(vp), vp, vq, vp * vp])
+    solvers on different paths differ by |M (a - b)|_k <= 2 tol S_k.  Rows
+    with some S_k = 0 (nothing to correct in that moment) are left out
+    explicitly; every compared multiplier must be finite."""
+    phi = phi_of(og)
     worst, wrow = 0.0, -1
     for r in range(len(a)):
         M = og.vol_uniform * (phi * xp[r]) @ phi.T
         S = og.vol_uniform * (np.abs(phi) * xp[r]).sum(1)
+        if not np.all(S > 0):
+            continue
+        assert np.all(np.isfinite(a[r])) and np.all(np.isfinite(b[r])), (r, a[r], b[r])
         e = np.max(np.abs(M @ (a[r] - b[r])) / S)
+        assert np.isfinite(e), r
         if e > worst:
             worst, wrow = e, r
     if worst > slack:
         print("lambda metric: worst %.3e at row %d: %s vs %s" % (worst, wrow, a[wrow], b[wrow]))
     return worst <= slack
+
+
+def level_check_value(og, x, xh, tau, alpha):
+    """max |f - x| / e of the oracle at one quantizer level (FP64), for a
+    single finite histogram: the value the end-to-end check compares with 1."""
+    codes, xp, _, _, st = oracle.quantize(x[None], xh[None], tau, alpha)
+    Q = oracle.moments(og, x[None])
+    lam, f, it, nst = oracle.newton(og, xp, Q)
+    return float(np.max(np.abs(f[0] - x) / (tau * x.max())))
+
+
+def expected_codes(og, x, xh, tau, st_gpu, ref):
+    """Codes every row must carry: the oracle's where the statuses agree; where
+    they differ, the oracle's quantizer at the level the GPU chose (all escape
+    codes for a verbatim row).  A status may differ only through the end-to-end
+    check's decision at a level whose check value is on the bound (within
+    1e-6): the two sides evaluate f in different arithmetic."""
+    want = ref["codes"].copy()
+    diff = np.nonzero(st_gpu != ref["status"])[0]
+    for r in diff:
+        flip = int(st_gpu[r]) ^ int(ref["status"][r])
+        assert flip & (oracle.ALPHA_RETRY | oracle.VERBATIM), (r, st_gpu[r], ref["status"][r])
+        lvl = 0.125 if (flip & oracle.ALPHA_RETRY) == 0 else 0.5
+        v = level_check_value(og, x[r], xh[r], tau, lvl)
+        assert abs(v - 1.0) <= 1e-6, (r, v, st_gpu[r], ref["status"][r])
+        if st_gpu[r] & oracle.VERBATIM:
+            want[r] = oracle.ESCAPE
+        else:
+            a = 0.125 if st_gpu[r] & oracle.ALPHA_RETRY else 0.5
+            want[r] = oracle.quantize(x[r][None], xh[r][None], tau, a)[0][0]
+    return want, diff
 
 
 def xprime_at_level(x, xh, tau, status):
@@ -199,22 +240,28 @@ def test_l2_variant_matches_oracle(aq, grids):
     assert lam_close(r["lam"].cpu().numpy(), lam_o)
 
 
-def check_batch(aq, og, x, xh, tau, kernel, n_expect_conv=0.95):
-    p = aq.params_default(tau=tau, kernel=kernel)
+def check_batch(aq, og, x, xh, tau, kernel, n_expect_conv=0.95, prm=None, oprm=None):
+    """quantize_correct against oracle.compress_correct on every row: codes
+    bit-exact (at the level each side chose), scales exact, statuses equal
+    except end-to-end-check flips proven to sit on the bound, multipliers in
+    the M-metric, every point within the bound, moments within 1e-10."""
+    p = prm or aq.params_default(tau=tau, kernel=kernel)
     out = aq.quantize_correct(aq_grid(aq), dev(x), dev(xh), p, outlier_capacity=64 * 1521,
                               want_f=True)
     torch.cuda.synchronize()
-    ref = oracle.compress_correct(og, x, xh, oracle.Params(tau=tau))
+    ref = oracle.compress_correct(og, x, xh, oprm or oracle.Params(tau=tau))
     st = out.status.cpu().numpy()
-    same = st == ref["status"]
-    assert same.mean() >= 0.99, (st[~same], ref["status"][~same])
+    want, diff = expected_codes(og, x, xh, tau, st, ref)
+    assert len(diff) <= max(2, len(x) // 1000), (len(diff), st[diff], ref["status"][diff])
     codes = out.codes.cpu().numpy()
-    assert np.array_equal(codes[same], ref["codes"][same])
+    bad = np.nonzero((codes != want).any(axis=1))[0]
+    assert len(bad) == 0, (bad[:8], st[bad[:8]], ref["status"][bad[:8]])
     assert np.array_equal(out.scale.cpu().numpy(), ref["scale"])
+    same = st == ref["status"]
     lam = out.lam.cpu().numpy()
     if kernel == aq.KERNEL_FP64:  # same iteration as the oracle: lambda agrees closely
         assert lam_close(lam[same], ref["lam"][same])
-    fin_rows = same & np.isfinite(x).all(axis=1)
+    fin_rows = same & np.isfinite(x).all(axis=1) & ((st & oracle.VERBATIM) == 0)
     xp = xprime_at_level(np.nan_to_num(x[fin_rows]), xh[fin_rows], tau,
                          ref["status"][fin_rows])
     assert lam_metric_close(lam[fin_rows], ref["lam"][fin_rows], xp, og)
@@ -225,7 +272,7 @@ def check_batch(aq, og, x, xh, tau, kernel, n_expect_conv=0.95):
     good = fin & (x.min(axis=1) >= 0) & (x.max(axis=1) > 0)
     S = oracle.abs_moments(og, x[good])
     assert np.all(np.abs(oracle.moments(og, f[good]) - oracle.moments(og, x[good])) <= 1e-10 * S)
-    assert np.mean((st & oracle.CONVERGED) != 0) >= n_expect_conv
+    assert np.mean((st & (oracle.CONVERGED | oracle.ROUND2)) != 0) >= n_expect_conv
     return out, ref
 
 
@@ -248,31 +295,53 @@ def test_quantize_correct_matches_oracle(aq, grids, n, tau, kernel):
     check_batch(aq, og, x, xh, tau, k, n_expect_conv=0.9)
 
 
-def test_fast_kernel_large_batch_matches_fp64_kernel(aq, grids):
-    """Several thousand histograms (many CTAs, ragged last wave): the fast and
-    the FP64 kernels agree on codes bit for bit and on lambda within tolerance."""
+@pytest.mark.parametrize("kernel", ["fast", "fp64"])
+def test_large_batch_matches_oracle(aq, grids, kernel):
+    """9,001 histograms: beyond the correction kernel's resident warps (at most
+    4 CTAs x 4 warps on each of the SMs), so warps take several histograms
+    each and the last wave is ragged; every row against the oracle."""
     _, og = grids
-    n = 3001
+    n = 9001
     x = synth.histograms(n, synth.config_seed(8))
     xh = synth.stand_in_xhat(x, 21)
-    outs = {}
-    for name, k in (("fp64", aq.KERNEL_FP64), ("fast", aq.KERNEL_FAST)):
-        p = aq.params_default(tau=1e-4, kernel=k)
-        outs[name] = aq.quantize_correct(aq_grid(aq), dev(x), dev(xh), p,
-                                         outlier_capacity=1 << 16, want_f=True)
+    k = aq.KERNEL_FP64 if kernel == "fp64" else aq.KERNEL_FAST
+    check_batch(aq, og, x, xh, 1e-4, k, n_expect_conv=0.99)
+
+
+def test_round2_success_path_matches_oracle_tilts(aq, grids):
+    """Tilts of order one defeat the undamped step of Eq. (6); round 2 (damped
+    Newton from zero) must return the closed-form tilt, as the oracle does."""
+    g, og = grids
+    n = 48
+    x = synth.histograms(n, synth.config_seed(0))
+    Q = oracle.moments(og, x)
+    rng = np.random.default_rng(5)
+    lam_t = rng.normal(0, 1, size=(n, 4)) * np.array([1.0, 0.5, 0.3, 0.2]) * 2.0
+    xp = x * np.exp(lam_t @ phi_of(og))
+    r = aq.qoi_correct(g, dev(xp), dev(Q), aq.params_default())
     torch.cuda.synchronize()
-    a, b = outs["fp64"], outs["fast"]
-    sa, sb = a.status.cpu().numpy(), b.status.cpu().numpy()
-    same = sa == sb
-    assert same.mean() >= 0.995
-    assert np.array_equal(a.codes.cpu().numpy()[same], b.codes.cpu().numpy()[same])
-    xp = xprime_at_level(x[same], xh[same], 1e-4, sa[same])
-    assert lam_metric_close(b.lam.cpu().numpy()[same], a.lam.cpu().numpy()[same], xp, og)
-    fb = b.f.cpu().numpy()
-    e = 1e-4 * x.max(axis=1, keepdims=True)
-    assert np.all(np.abs(fb - x) <= e)
-    S = oracle.abs_moments(og, x)
-    assert np.all(np.abs(oracle.moments(og, fb) - oracle.moments(og, x)) <= 1e-10 * S)
+    lam_o, f_o, it_o, st_o = oracle.newton(og, xp, Q)
+    st = r["status"].cpu().numpy()
+    assert np.array_equal(st, st_o)
+    assert np.sum(st == oracle.ROUND2) >= 10
+    lam = r["lam"].cpu().numpy()
+    assert np.all(np.abs(lam - lam_t) <= 1e-11 * (1 + np.abs(lam_t)))
+    assert lam_metric_close(lam, lam_o, xp, og)
+
+
+@pytest.mark.parametrize("kernel", ["fast", "fp64"])
+def test_round2_inside_quantize_correct_matches_oracle(aq, grids, kernel):
+    """Round 1 capped at one step: most histograms go to round 2, in the FP64
+    kernel (the fast kernel hands them over); codes, statuses and multipliers
+    against the oracle with the same cap."""
+    _, og = grids
+    x, xh = special_batch(96, 17, 1e-4)
+    k = aq.KERNEL_FP64 if kernel == "fp64" else aq.KERNEL_FAST
+    p = aq.params_default(tau=1e-4, kernel=k, max_iter=1, warm_iters=1)
+    out, ref = check_batch(aq, og, x, xh, 1e-4, k, n_expect_conv=0.9, prm=p,
+                           oprm=oracle.Params(tau=1e-4, max_iter=1))
+    st = out.status.cpu().numpy()
+    assert np.sum((st & oracle.ROUND2) != 0) >= 48
 
 
 def test_quantize_correct_verbatim_and_zero(aq, grids):
@@ -308,3 +377,61 @@ def test_empty_batch_is_a_noop(aq, grids):
     x = torch.empty((0, 1521), dtype=torch.float64, device=DEV)
     Q = aq.qoi_moments(g, x)
     assert Q.shape == (0, 4)
+
+
+def biased_xhat(x, tau, pattern, og):
+    """Decoded histograms that leave residuals of a chosen sign pattern
+    (rho Delta, |rho| <= 0.45): large moment defects, so the multipliers reach
+    the fast kernel's limits (|lambda.phi| up to 0.05, |H| up to 1e-5 S)."""
+    v = np.tile(og.vpar, len(og.vperp)) / 4.0
+    rho = {"cubic": 0.45 * v ** 3, "quad": 0.45 * (2 * v * v - 1),
+           "const": 0.45 * np.ones_like(v)}[pattern]
+    dl = np.array([oracle.delta(tau * s, 0.5) for s in x.max(axis=1)])
+    xh = np.zeros((len(x), 1536), np.float32)
+    xh[:, :x.shape[1]] = (x - rho[None, :] * dl[:, None]).astype(np.float32)
+    return xh
+
+
+@pytest.mark.parametrize("tau,pattern", [(1e-3, "cubic"), (3e-3, "cubic"), (3e-3, "quad"),
+                                         (3e-3, "const"), (1e-2, "const")])
+def test_fast_kernel_converged_means_residual_below_tol(aq, grids, tau, pattern):
+    """Every histogram the fast kernel reports converged has |g_k| <= 1e-12 S_k
+    (reading of the stopping rule: S_k = sum vol |phi_k| f at the final
+    lambda), recomputed here in FP64 from its multipliers with exactly
+    rounded sums (math.fsum): the kernel's truncated series for h(t), its FP32
+    sums and its certified last step must all be inside the bound.  The
+    inputs sit near the kernel's limits (checked: some rows reach
+    |lambda.phi| > 0.02 and |H| > 3e-6 S)."""
+    import math
+    _, og = grids
+    x = synth.histograms(64, synth.config_seed(0) + 50)
+    xh = biased_xhat(x, tau, pattern, og)
+    p = aq.params_default(tau=tau, kernel=aq.KERNEL_FAST)
+    out = aq.quantize_correct(aq_grid(aq), dev(x), dev(xh), p, want_f=True)
+    torch.cuda.synchronize()
+    st = out.status.cpu().numpy()
+    lam = out.lam.cpu().numpy()
+    codes = out.codes.cpu().numpy()
+    phi = phi_of(og)
+    vol = og.vol_uniform
+    reach_t, reach_h = 0.0, 0.0
+    for b in np.nonzero(st & oracle.CONVERGED)[0]:
+        a = 0.125 if st[b] & oracle.ALPHA_RETRY else 0.5
+        qc, xp, _, _, _ = oracle.quantize(x[b][None], xh[b][None], tau, a)
+        assert np.array_equal(qc[0], codes[b]), b
+        xp = xp[0]
+        t = lam[b] @ phi
+        f = xp * np.exp(-t)
+        for k in range(4):
+            gk = math.fsum(vol * phi[k] * (f - x[b]))
+            Sk = math.fsum(vol * np.abs(phi[k]) * f)
+            assert abs(gk) <= (1e-12 + 1e-15) * Sk, (b, k, abs(gk) / Sk)
+        pos = xp > 0
+        reach_t = max(reach_t, float(np.abs(t[pos]).max()))
+        h = np.expm1(-t) + t
+        Hs = np.abs(vol * (phi * xp * h).sum(1)) / (vol * (np.abs(phi) * xp).sum(1))
+        if np.abs(t[pos]).max() <= 0.05 and Hs.max() <= 1e-5:
+            reach_h = max(reach_h, float(Hs.max()))
+    assert np.mean((st & oracle.CONVERGED) != 0) >= 0.9
+    if (tau, pattern) == (3e-3, "quad"):
+        assert reach_t > 0.02 and reach_h > 3e-6, (reach_t, reach_h)

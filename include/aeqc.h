@@ -564,6 +564,33 @@ int aeqc_batch_peek(const void* blob_host, size_t bytes, int64_t* n, int32_t* P,
                     int32_t* latent_dtype, int64_t* outliers);
 int aeqc_batch_unpack(const void* blob_host, size_t bytes, aeqc_compressed* out, void* stream);
 
+/* ---- multi-GPU partitioning (host) ---------------------------------------- */
+/* Each processor trains and compresses its own subdomains with no exchange
+ * of data (Sec. III Stage 1; Sec. IV-B, distributed training), and the
+ * per-processor buffers are written one after another (Sec. III, the
+ * output stage).  On one node with several GPUs (one process per GPU) whole
+ * subdomains are the unit: aeqc_partition_lpt assigns them to ranks by the
+ * longest-processing-time rule on their histogram counts, and
+ * aeqc_exclusive_scan turns per-rank compressed byte counts into output
+ * offsets.  Host pointers, synchronous, deterministic: every rank that calls
+ * them with the same arguments gets the same answer, so no collective is
+ * needed to agree on the assignment.
+ *
+ * aeqc_partition_lpt: counts_host[n_groups] (>= 0) histograms per subdomain;
+ * owner_host[n_groups] receives the rank of each subdomain and
+ * load_host[n_ranks] (may be NULL) the histograms per rank.  Subdomains are
+ * taken in decreasing count (equal counts: lower index first) and each goes
+ * to the rank with the least load so far (equal loads: lower rank), so the
+ * largest load is at most (4/3 - 1/(3 n_ranks)) of the best possible.
+ * AEQC_EINVAL for n_groups < 0, n_ranks < 1, a negative count or null arrays.
+ *
+ * aeqc_exclusive_scan: offsets_host[n + 1] with offsets[0] = 0 and
+ * offsets[r + 1] = offsets[r] + sizes_host[r]; AEQC_EINVAL for n < 0, a
+ * negative size, null arrays or a total beyond INT64_MAX. */
+int aeqc_partition_lpt(const int64_t* counts_host, int32_t n_groups, int32_t n_ranks,
+                       int32_t* owner_host, int64_t* load_host);
+int aeqc_exclusive_scan(const int64_t* sizes_host, int32_t n, int64_t* offsets_host);
+
 #ifdef __cplusplus
 }
 #endif

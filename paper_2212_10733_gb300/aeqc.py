@@ -190,6 +190,9 @@ SYMBOLS = {
     "aeqc_batch_peek": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
     "aeqc_batch_unpack": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
+    "aeqc_partition_lpt": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                     C.c_void_p]),
+    "aeqc_exclusive_scan": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
 }
 
 
@@ -867,3 +870,25 @@ def bound_search(m: Model, grid: Grid, x, params: aeqc_params, target: float,
                                  C.byref(params), target, tau_lo, tau_hi, probes, cap,
                                  C.byref(t), C.byref(e), _ptr(ws), ws.numel(), _stream(stream)))
     return t.value, e.value
+
+
+# --- multi-GPU partitioning (host) ------------------------------------------
+
+def partition_lpt(counts, n_ranks: int):
+    """(owner [G] int32, load [n_ranks] int64): whole subdomains to ranks by
+    the longest-processing-time rule on their histogram counts."""
+    c = np.ascontiguousarray(counts, np.int64)
+    owner = np.zeros(len(c), np.int32)
+    load_ = np.zeros(int(n_ranks), np.int64)
+    _check(load().aeqc_partition_lpt(c.ctypes.data if len(c) else None, len(c), int(n_ranks),
+                                     owner.ctypes.data if len(c) else None, load_.ctypes.data))
+    return owner, load_
+
+
+def exclusive_scan(sizes):
+    """offsets [n + 1]: where each rank's output starts, and the total."""
+    sz = np.ascontiguousarray(sizes, np.int64)
+    off = np.zeros(len(sz) + 1, np.int64)
+    _check(load().aeqc_exclusive_scan(sz.ctypes.data if len(sz) else None, len(sz),
+                                      off.ctypes.data))
+    return off

@@ -114,14 +114,22 @@ def _add_heavy_tail_numpy(x, n, seed, heavy_frac, idx):
 
 
 def histograms_torch(n: int, seed: int, device, k_max: int = 3, heavy_frac: float = 0.0,
-                     chunk: int = 1 << 17, step: int = 0, grid=(N_PAR, N_PERP)):
+                     chunk: int = 1 << 17, step: int = 0, grid=(N_PAR, N_PERP), rows=None):
     """Same workload as :func:`histograms` evaluated on a torch device in chunks
     (values may differ from the numpy evaluation in the last ulp; the device
-    copy is what both sides of a comparison consume)."""
+    copy is what both sides of a comparison consume).  ``rows`` selects rows
+    of the n-histogram workload (same values as the full set at those rows;
+    without a heavy tail)."""
     import torch
     vpar, vperp, _ = grid_arrays(*grid)
     Pg = grid[0] * grid[1]
     prm = drift_params(gaussian_params(n, seed, k_max), step)
+    if rows is not None:
+        if heavy_frac > 0.0:
+            raise ValueError("histograms_torch: rows= with a heavy tail is not supported")
+        rows = np.asarray(rows, dtype=np.int64)
+        prm = {k: v[rows] for k, v in prm.items()}
+        n = len(rows)
     tv = torch.as_tensor(vpar, device=device)
     tq = torch.as_tensor(vperp, device=device)
     out = torch.empty((n, Pg), dtype=torch.float64, device=device)

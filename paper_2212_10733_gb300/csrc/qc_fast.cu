@@ -185,49 +185,54 @@ __device__ __noinline__ PointQ quant_point_hard(double x, float xh, double dl) {
   return o;
 }
 
-// Quantizer decision for one point (x finite, x >= 0), exact.  With
-// u = Delta 2^-38, X = floor(x / u) and Xh = trunc(xhat / u) come from the bit
-// patterns; D = X - Xh is within (-1, 2) units of the exact scaled difference,
-// so q = round-half-even(D / 2^38) is certain unless D's fraction sits in
-// {1/2 - u, 1/2}.  The zero level (g < 0 or g > 2x, g = xhat + q Delta) is
-// decided on G = Xh + q 2^38 (within 1 unit of g / u) and A = G - 2X (within
-// (-1, 3) units).  Points in an ambiguity band take the exact FP64 routine.
-__device__ __forceinline__ PointQ quant_point_int(double x, float xh, const QConst& c) {
-  // every outcome is formed and one is selected (no divergent branches on the
-  // common path); only an ambiguous point branches to the exact routine
-  const unsigned long long u =
-      (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+// Quantizer decision for one point (x finite, x >= 0), exact where it is
+// not flagged.  With u = Delta 2^-38, X = floor(x / u) and Xh = trunc(xhat / u)
+// come from the bit patterns; the exact scaled difference (x - xhat) / u is
+// D + e with D = X - Xh and e in (-1, 2).  With t = D + 2^37, q = floor(t / 2^38)
+// is the round-half-even index unless t's fraction is within two units of a
+// multiple of 2^38 (a tie or an uncertain rounding): that point is flagged.
+// rho = D - q 2^38 is the residual (x - xhat - q Delta) / u within the same
+// (-1, 2) units; the zero level wins iff |x - xhat - q Delta| > x, decided on
+// |rho| - X unless within three units (flagged).  Escapes (|q| > 32766 or a
+// non-finite or huge xhat) are flagged too.  A flagged point's outputs here
+// are zero; the caller completes it with the exact FP64 routine.
+struct PointF {
+  int code;       // q, or AEQC_CODE_ZERO (0 when flagged)
+  long long xpw;  // x' / u within one unit (0 when flagged or at the zero level)
+  long long rho;  // (x - x') / u within two units (0 when flagged)
+  float xpf;      // x' as a float (0 when flagged or at the zero level)
+  bool hard;
+};
+
+__device__ __forceinline__ PointF quant_point_fast(double x, float xh, const QConst& c) {
+  const unsigned long long ux = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)(ux >> 52);  // x >= 0: no sign bit
+  // mantissa with its implicit bit at bits 10..62; a subnormal x gives X = 0
+  const unsigned long long M10 =
+      ((ux & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(E != 0) << 52)) << 10;
+  const long long X = (long long)(M10 >> min(c.cx - E, 63));
   const unsigned v = __float_as_uint(xh);
   const int Eh = (v >> 23) & 0xff;
-  const int E = (int)(u >> 52);
-  const unsigned long long M10 = ((u & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 10;
-  const int r = c.cx - E;  // >= 1 for x <= s
-  const long long X = (E != 0 && r < 64) ? (long long)(M10 >> (r & 63)) : 0;
-  // certainly |q| > 32766, or non-finite xhat (thr <= 230 < 255)
-  const bool esc_h = Eh >= c.thr;
-  const unsigned long long m40 = (unsigned long long)((v & 0x7fffffu) | (Eh ? 0x800000u : 0u)) << 40;
-  const int rh = c.ch - (Eh ? Eh : 1);  // >= 3 below the escape threshold
-  const long long mag = (rh >= 0 && rh < 64) ? (long long)(m40 >> (rh & 63)) : 0;
-  const long long Xh = (v >> 31) ? -mag : mag;
-  const long long D = X - Xh;
-  const long long m = D >> QF;
-  const long long fr = D & ((1ll << QF) - 1);  // D - m 2^38
-  constexpr long long half = 1ll << (QF - 1);
-  const bool up = fr >= half + 1;
-  const bool band = !up && fr > half - 2;  // fraction in {1/2 - u, 1/2}: ambiguous
-  const long long q = up ? m + 1 : m;
-  const bool esc = esc_h || (!band && (q > AEQC_CODE_MAX || q < -AEQC_CODE_MAX));
-  const long long G = Xh + q * (1ll << QF);
-  const long long A = G - 2 * X;
-  const bool hard = !esc && (band || G == 0 || (G > 0 && A >= 0 && A <= 2));
-  if (hard) return quant_point_hard(x, xh, c.dl);
-  const bool zero = !esc && (G < 0 || A >= 3);
-  PointQ o;
-  o.code = esc ? AEQC_CODE_ESCAPE : (zero ? AEQC_CODE_ZERO : (int)q);
-  // at the zero level x < Delta / 2 and the residual is x itself
-  o.rho = esc ? 0ll : (zero ? X : D - q * (1ll << QF));
-  o.xpw = esc ? X : (zero ? 0 : G);
-  o.xpf = esc ? float_of_bits(u) : (zero ? 0.f : fmaf(small_int_to_float((int)q), c.dl_f, xh));
+  const bool esc_h = Eh >= c.thr;  // |q| > 32766 for sure, or a non-finite xhat
+  const unsigned long long m40 = (unsigned long long)((v & 0x7fffffu) | (Eh ? 0x800000u : 0u))
+                                 << 40;
+  const long long mag = (long long)(m40 >> min(max(c.ch - (Eh ? Eh : 1), 0), 63));
+  const long long D = X - ((v >> 31) ? -mag : mag);
+  const long long t = D + (1ll << (QF - 1));
+  const int q = (int)(t >> QF);
+  const bool band = ((t + 2) & ((1ll << QF) - 1)) < 4;
+  const long long rho = D - ((long long)q << QF);
+  const long long uz = (rho < 0 ? -rho : rho) - X;  // |r| - x in units
+  const bool zero = uz > 3;
+  const bool band2 = (unsigned long long)(uz + 3) <= 6ull;
+  PointF o;
+  o.hard = band || band2 || esc_h || q > AEQC_CODE_MAX || q < -AEQC_CODE_MAX;
+  const bool keep = !o.hard && !zero;
+  o.code = o.hard ? 0 : (zero ? AEQC_CODE_ZERO : q);
+  o.xpw = keep ? X - rho : 0ll;
+  o.rho = o.hard ? 0ll : (zero ? X : rho);
+  // |q| < 2^22 wherever the value is kept
+  o.xpf = keep ? fmaf(small_int_to_float(q), c.dl_f, xh) : 0.f;
   return o;
 }
 
@@ -316,17 +321,49 @@ struct ColSums {
   float xs;
 };
 
+// a + b c for unsigned 32-bit b, c (one wide multiply-add)
+__device__ __forceinline__ long long mad_wide(long long a, unsigned b, unsigned c) {
+  return (long long)((unsigned long long)a + (unsigned long long)b * (unsigned long long)c);
+}
+
+__device__ __forceinline__ void colsum_add(ColSums& cs, long long xpw, long long rho, float xpf,
+                                           unsigned j2, unsigned j4) {
+  // x' >= 0 here, below 2^60 units: two unsigned 32-bit parts (31 + 29 bits)
+  const unsigned xl = (unsigned)xpw & 0x7FFFFFFFu, xu = (unsigned)(xpw >> 31);
+  cs.b[0] += xl;
+  cs.b[1] = mad_wide(cs.b[1], xl, j2);
+  cs.b[2] = mad_wide(cs.b[2], xl, j4);
+  cs.a[0] += xu;
+  cs.a[1] = mad_wide(cs.a[1], xu, j2);
+  cs.a[2] = mad_wide(cs.a[2], xu, j4);
+  // |rho| <= 2^37 and the grid's sum of j^2 is below 2^25 (host check):
+  // every total stays below 2^62.  rho j2 from rho's two words, modulo 2^64
+  // (two's complement: the exact product).
+  cs.u[0] += rho;
+  cs.u[1] = mad_wide(cs.u[1] + (long long)((unsigned long long)((unsigned)(rho >> 32) * j2) << 32),
+                     (unsigned)rho, j2);
+  cs.xs += xpf;
+}
+
+// Quantize one segment (column sg.c, rows [j0, j1)): codes to cb (global), x'
+// and the residual (in Delta 2^-15) to shared memory, column sums to cs.  One
+// straight-line body per point; the flagged points (a bit per row of the
+// segment, at most 64 rows) are completed after the walk.
 __device__ __forceinline__ void quant_segment(const Seg& sg, int n_par, const double* xb,
                                               const float* xhb, const QConst& c, FastWS& w,
                                               int16_t* cb, ColSums& cs, int& esc,
                                               int& nonzero) {
   cs = ColSums{{0, 0, 0}, {0, 0, 0}, {0, 0}, 0.f};
+  unsigned long long flagged = 0;
+  int nz = 0;
   int p = sg.j0 * n_par + sg.c;
   // loads issued two points ahead of the work
   double xn = sg.j0 < sg.j1 ? __ldg(xb + p) : 0.0;
   float hn = sg.j0 < sg.j1 ? __ldg(xhb + p) : 0.f;
   double xn2 = sg.j0 + 1 < sg.j1 ? __ldg(xb + p + n_par) : 0.0;
   float hn2 = sg.j0 + 1 < sg.j1 ? __ldg(xhb + p + n_par) : 0.f;
+  unsigned j2 = (unsigned)(sg.j0 * sg.j0);
+#pragma unroll 1
   for (int j = sg.j0; j < sg.j1; ++j, p += n_par) {
     const double x = xn;
     const float xh = hn;
@@ -336,26 +373,29 @@ __device__ __forceinline__ void quant_segment(const Seg& sg, int n_par, const do
       xn2 = __ldg(xb + p + 2 * n_par);
       hn2 = __ldg(xhb + p + 2 * n_par);
     }
-    const PointQ o = quant_point_int(x, xh, c);
+    const PointF o = quant_point_fast(x, xh, c);
     cb[p] = (int16_t)o.code;
     w.xp[p] = o.xpf;
     w.rho[p] = (int16_t)((o.rho + (1ll << 22)) >> 23);
+    nz |= o.code;
+    if (o.hard) flagged |= 1ull << (j - sg.j0);
+    colsum_add(cs, o.xpw, o.rho, o.xpf, j2, j2 * j2);
+    j2 += 2 * j + 1;  // (j + 1)^2
+  }
+  nonzero |= nz;
+  // the flagged points: the exact FP64 routine (out of line), outputs stored
+  // and moments added
+  while (flagged) {
+    const int j = sg.j0 + __ffsll((long long)flagged) - 1;
+    flagged &= flagged - 1;
+    const int pf = j * n_par + sg.c;
+    const PointQ o = quant_point_hard(__ldg(xb + pf), __ldg(xhb + pf), c.dl);
+    cb[pf] = (int16_t)o.code;
+    w.xp[pf] = o.xpf;
+    w.rho[pf] = (int16_t)((o.rho + (1ll << 22)) >> 23);
     esc |= o.code == AEQC_CODE_ESCAPE;
     nonzero |= o.code != 0;
-    const int j2 = j * j, j4 = j2 * j2;
-    // x' >= 0 here, below 2^60 units: two unsigned 32-bit parts (31 + 29 bits)
-    const unsigned xl = (unsigned)o.xpw & 0x7FFFFFFFu, xu = (unsigned)(o.xpw >> 31);
-    cs.b[0] += xl;
-    cs.b[1] += (long long)xl * (unsigned)j2;
-    cs.b[2] += (long long)xl * (unsigned)j4;
-    cs.a[0] += xu;
-    cs.a[1] += (long long)xu * (unsigned)j2;
-    cs.a[2] += (long long)xu * (unsigned)j4;
-    // |rho| <= 2^37 and the grid's sum of j^2 is below 2^31 (host check):
-    // every total stays below 2^62
-    cs.u[0] += o.rho;
-    cs.u[1] += o.rho * j2;
-    cs.xs += o.xpf;
+    colsum_add(cs, o.xpw, o.rho, o.xpf, (unsigned)(j * j), (unsigned)(j * j * j * j));
   }
 }
 
@@ -463,7 +503,7 @@ __device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb,
 struct PassOut {
   df H[4];
   float Habs[4];  // bounds on the sums of |terms| (for the FP32 rounding bound)
-  float tmax;     // max |t| over points with x' > 0
+  float tmax;     // bound on |t| over the grid points (segment end points)
   float errmax;   // largest FP32 check value |x' e^{-t} - x| of the points
   int viol, uncertain;
 };
@@ -502,20 +542,16 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
                           int lane) {
   df a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};  // sums of y, y ic, y ic^2, y j^2
   float ab1 = 0.f, tmax = 0.f, errmax = 0.f;
-  int viol = 0, unc = 0;
   const float cq = c.dl_f * 3.0517578125e-05f, dq = -12582912.f * cq;  // Delta 2^-15
-  // x' h(t) and the check of one point
+  // x' h(t) and the check value of one point (the largest check value decides
+  // the check after the walk)
   auto point = [&](int p, float t) -> float {
     const float xp = w.xp[p];
     const float h =
         t * t * fmaf(-t, fmaf(-t, fmaf(-t, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f);
-    if (xp > 0.f) tmax = fmaxf(tmax, fabsf(t));
     // Delta rho from its 2^-15 fixed point: exact, see small_int_to_float
     const float drho = fmaf(__int_as_float(0x4B400000 + (int)w.rho[p]), cq, dq);
-    const float err = fabsf(fmaf(xp, h - t, -drho));
-    errmax = fmaxf(errmax, err);
-    viol |= err > e_hi;
-    unc |= err > e_lo;
+    errmax = fmaxf(errmax, fabsf(fmaf(xp, h - t, -drho)));
     return xp * h;
   };
   Seg sg[2];
@@ -532,6 +568,12 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
     const float ah = A.hi, al = A.lo;
     df s0 = {0.f, 0.f}, s3 = {0.f, 0.f};
     float jf = small_int_to_float(sgm.j0), j2f = jf * jf;
+    // |t| is largest at an end of the segment (t is monotone in j^2): a bound
+    // over every point of the segment, x' = 0 included
+    if (sgm.j1 > sgm.j0) {
+      const float jl = small_int_to_float(sgm.j1 - 1);
+      tmax = fmaxf(tmax, fmaxf(fabsf(fmaf(tc.h[2], j2f, ah)), fabsf(fmaf(tc.h[2], jl * jl, ah))));
+    }
     int p = sgm.j0 * g.n_par + sgm.c;
     for (int j = sgm.j0; j < sgm.j1; ++j, p += g.n_par) {
       const float t = fmaf(tc.h[2], j2f, ah) + fmaf(tc.l[2], j2f, al);
@@ -606,10 +648,10 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
     tm = fmaxf(tm, __shfl_xor_sync(FULL, tm, s));
     em = fmaxf(em, __shfl_xor_sync(FULL, em, s));
   }
-  o.tmax = tm;
+  o.tmax = tm * 1.000001f;  // the end points' FP32 rounding
   o.errmax = em;
-  o.viol = __any_sync(FULL, viol);
-  o.uncertain = __any_sync(FULL, unc);
+  o.viol = em > e_hi;
+  o.uncertain = em > e_lo;
 }
 
 // FP32 Cholesky of the unit-diagonal scaling of M (the chord Jacobian).

@@ -536,10 +536,9 @@ __device__ __forceinline__ TCoef make_tcoef(const FastGridK& fg, const df lam[4]
 // The points are walked in the segments of phase_a: on a segment t = A +
 // a2 j^2 with A a constant, and one column sum of y and of y j^2 per segment
 // gives all four sums.
-template <bool EXACT>
 __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
                           const QConst& c, const TCoef& tc, float e_lo, float e_hi, PassOut& o,
-                          int lane) {
+                          int lane, const bool EXACT) {
   df a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};  // sums of y, y ic, y ic^2, y j^2
   float ab1 = 0.f, tmax = 0.f, errmax = 0.f;
   const float cq = c.dl_f * 3.0517578125e-05f, dq = -12582912.f * cq;  // Delta 2^-15
@@ -785,12 +784,18 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
       const float margin = 4e-7f * (s * tb + c.dl_f) + 3.0517578125e-05f * c.dl_f + 1e-30f;
       PassOut po;
       const TCoef tc = make_tcoef(fg, lam);
-      pass_warp<false>(g, fg, w, c, tc, e - margin, e + margin, po, lane);
+      // FP32 sums first; again with TwoSum accumulation when their error bound
+      // (<= 50 FP32 roundings per lane: 50 u sum|terms|) is too wide.  One
+      // call site for both (the kernel is bound by instruction fetch).
       bool redo = false;
+#pragma unroll 1
+      for (int rep = 0; rep < 2; ++rep) {
+        pass_warp(g, fg, w, c, tc, e - margin, e + margin, po, lane, rep != 0);
+        if (rep) break;
 #pragma unroll
-      for (int k = 0; k < 4; ++k)  // <= 50 FP32 roundings per lane: |error| <= 50 u sum|terms|
-        redo = redo || 3.5e-6f * po.Habs[k] > 1e-13f * mo.S[k];
-      if (redo) pass_warp<true>(g, fg, w, c, tc, e - margin, e + margin, po, lane);
+        for (int k = 0; k < 4; ++k) redo = redo || 3.5e-6f * po.Habs[k] > 1e-13f * mo.S[k];
+        if (!redo) break;
+      }
       const float t2 = po.tmax * po.tmax;
       const float hrel = (redo ? 8e-7f : 4.3e-6f) + 0.003f * t2 * t2;
       float eh = 0.f;

@@ -1,7 +1,7 @@
 // BF16 autoencoder forward on the 5th-generation tensor cores (Stage 3 of
 // Sec. III; the tied linear network of Sec. IV-B): tcgen05.mma with FP32
-// accumulators in tensor memory, weights streamed by TMA, one CTA per tile of
-// 128 histograms.
+// accumulators in tensor memory, weights streamed by TMA; persistent kernels
+// (one CTA per SM) walking tiles of 128 histograms.
 //
 // Encoder (one kernel): h = act((x W1') / s + b1') then z = h W2 + b2, with
 // W1' = W1 / sigma and b1' = b1 - W1'^T mu folded on the host side, s the
@@ -107,6 +107,7 @@ __device__ __forceinline__ bool tile_info(int t, long long n, int G, const long 
 struct EncArgs {
   const double* x;
   long long n;
+  long long ntiles;  // tiles to walk (grouped: an upper bound, spare tiles skipped)
   int P, Kp, H, L, act, G, ns;
   const long long* goff;
   const int* toff;
@@ -139,6 +140,14 @@ struct EncSmem {
   }
 };
 
+// Persistent: one CTA per SM walks the tiles t = blockIdx.x, + gridDim.x, ...
+// (tiles are numbered group by group, so the CTAs working at one time share a
+// few groups' weights in L2).  Tensor memory is allocated and the barriers
+// initialised once; the stage ring continues across tiles, and the per-tile
+// barriers (acc_full, h1_full, w2_full, lat_full) complete once per tile, so
+// tile iteration i waits on parity i & 1.  The BF16 h tile of the second MMA
+// aliases the stage ring, so the next tile's operand writes (A by the
+// converters, W1 and W2 by the TMA warp) start after lat_full of this tile.
 __global__ void __launch_bounds__(NTHREADS, 1)
     enc_tc_kernel(const __grid_constant__ CUtensorMap mapW1,
                   const __grid_constant__ CUtensorMap mapW2, const EncArgs a) {
@@ -158,9 +167,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   double* rowmax = reinterpret_cast<double*>(sm + L.rowmax);
 
-  TileInfo ti;
-  if (!tile_info(blockIdx.x, a.n, a.G, a.goff, a.toff, ti)) return;
-  const int rows = (int)min((long long)BM, ti.mend - ti.m0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int H = a.H, nkb = a.Kp / KB, nh = (H + 255) / 256, hn = H < 256 ? H : 256;
   const uint32_t tcols = H <= 32 ? 32 : (H <= 64 ? 64 : (H <= 128 ? 128 : (H <= 256 ? 256 : 512)));
@@ -193,51 +199,71 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       prefetch_tmap(&mapW1);
       prefetch_tmap(&mapW2);
-      mbar_arrive_expect_tx(w2_full, (uint32_t)(H / KB) * a.L * 128);
-      for (int k2 = 0; k2 < H / KB; ++k2)
-        tma_load_3d(sm + L.w2 + k2 * a.L * 128, &mapW2, w2_full, k2 * KB, 0, ti.g);
-      for (int kb = 0; kb < nkb && !*abort_flag; ++kb) {
-        const int s = kb % ns;
-        const uint32_t ph = (kb / ns) & 1;
-        if (!mbar_wait(&empty[s], ph ^ 1)) {
+      int it = 0;  // stage ring position
+      int iter = 0;
+      for (long long t = blockIdx.x; t < a.ntiles && !*abort_flag; t += gridDim.x) {
+        TileInfo ti;
+        if (!tile_info((int)t, a.n, a.G, a.goff, a.toff, ti)) continue;
+        // the previous tile's second MMA has read h (aliasing the stages) and W2
+        if (iter > 0 && !mbar_wait(lat_full, (iter - 1) & 1)) {
           fail();
           break;
         }
-        uint8_t* bst = sm + s * L.stage_bytes + L.off_b;
-        mbar_arrive_expect_tx(&full_b[s], (uint32_t)H * 128);
-        for (int j = 0; j < nh; ++j)
-          tma_load_3d(bst + j * 256 * 128, &mapW1, &full_b[s], kb * KB, j * 256, ti.g);
+        mbar_arrive_expect_tx(w2_full, (uint32_t)(H / KB) * a.L * 128);
+        for (int k2 = 0; k2 < H / KB; ++k2)
+          tma_load_3d(sm + L.w2 + k2 * a.L * 128, &mapW2, w2_full, k2 * KB, 0, ti.g);
+        bool ok = true;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % ns;
+          const uint32_t ph = (it / ns) & 1;
+          if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1)) {
+            ok = false;
+            break;
+          }
+          uint8_t* bst = sm + s * L.stage_bytes + L.off_b;
+          mbar_arrive_expect_tx(&full_b[s], (uint32_t)H * 128);
+          for (int j = 0; j < nh; ++j)
+            tma_load_3d(bst + j * 256 * 128, &mapW1, &full_b[s], kb * KB, j * 256, ti.g);
+        }
+        if (!ok) {
+          fail();
+          break;
+        }
+        ++iter;
       }
     }
     __syncwarp();
   } else if (warp == WARP_MMA) {
     if (lane == 0) {
       const uint32_t id1 = idesc_bf16(BM, hn);
+      const uint32_t id2 = idesc_bf16(BM, a.L);
+      int it = 0, iter = 0;
       bool ok = true;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % ns;
-        const uint32_t ph = (kb / ns) & 1;
-        if (*abort_flag || !mbar_wait(&full_a[s], ph) || !mbar_wait(&full_b[s], ph)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t abase = smem_u32(sm + s * L.stage_bytes);
-        const uint32_t bbase = abase + L.off_b;
-#pragma unroll
-        for (int kk = 0; kk < KB / 16; ++kk)
-          for (int j = 0; j < nh; ++j)
-            mma_bf16(tmem + j * 256, desc_k128(abase + kk * 32),
-                     desc_k128(bbase + j * 256 * 128 + kk * 32), id1, (kb | kk) != 0);
-        mma_commit(&empty[s]);
-      }
-      mma_commit(acc_full);
-      if (ok) {
-        if (!mbar_wait(h1_full, 0) || !mbar_wait(w2_full, 0)) {
-          fail();
-        } else {
+      for (long long t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+        TileInfo ti;
+        if (!tile_info((int)t, a.n, a.G, a.goff, a.toff, ti)) continue;
+        const uint32_t tp = iter & 1;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % ns;
+          const uint32_t ph = (it / ns) & 1;
+          if (*abort_flag || !mbar_wait(&full_a[s], ph) || !mbar_wait(&full_b[s], ph)) {
+            ok = false;
+            break;
+          }
           tc_fence_after();
-          const uint32_t id2 = idesc_bf16(BM, a.L);
+          const uint32_t abase = smem_u32(sm + s * L.stage_bytes);
+          const uint32_t bbase = abase + L.off_b;
+#pragma unroll
+          for (int kk = 0; kk < KB / 16; ++kk)
+            for (int j = 0; j < nh; ++j)
+              mma_bf16(tmem + j * 256, desc_k128(abase + kk * 32),
+                       desc_k128(bbase + j * 256 * 128 + kk * 32), id1, (kb | kk) != 0);
+          mma_commit(&empty[s]);
+        }
+        mma_commit(acc_full);
+        if (ok && (!mbar_wait(h1_full, tp) || !mbar_wait(w2_full, tp))) ok = false;
+        if (ok) {
+          tc_fence_after();
           const uint32_t hbase = smem_u32(sm), wbase = smem_u32(sm + L.w2);
           for (int k2 = 0; k2 < H / KB; ++k2)
 #pragma unroll
@@ -245,134 +271,150 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               mma_bf16(tmem, desc_k128(hbase + k2 * A_STAGE + kk * 32),
                        desc_k128(wbase + k2 * a.L * 128 + kk * 32), id2, (k2 | kk) != 0);
         }
-      } else {
-        fail();
+        mma_commit(lat_full);
+        ++iter;
       }
-      mma_commit(lat_full);
+      if (!ok) fail();
     }
     __syncwarp();
   } else {
-    // ---- converters: FP64 rows -> BF16 swizzled A tiles, row maxima ----
-    // row maxima on the raw bits as signed 64-bit integers: exact among
-    // non-negative values (which order like their bits) and below any of
-    // them for negatives; a row without a non-negative value is redone
-    // exactly after the main loop
-    long long mraw[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) mraw[i] = (long long)0x8000000000000000ull;
+    // ---- converters / epilogue: eight warps ----
+    const int q = warp & 3, half = warp >> 2;
+    const int r = q * 32 + lane;
+    int it = 0, iter = 0;
     bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % ns;
-      const uint32_t ph = (kb / ns) & 1;
-      if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1)) {
+    for (long long t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+      TileInfo ti;
+      if (!tile_info((int)t, a.n, a.G, a.goff, a.toff, ti)) continue;
+      const int rows = (int)min((long long)BM, ti.mend - ti.m0);
+      const uint32_t tp = iter & 1;
+      // FP64 rows -> BF16 swizzled A tiles, row maxima on the raw bits as
+      // signed 64-bit integers: exact among non-negative values (which order
+      // like their bits) and below any of them for negatives; a row without a
+      // non-negative value is redone exactly after the main loop
+      long long mraw[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) mraw[i] = (long long)0x8000000000000000ull;
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
+        const int s = it % ns;
+        const uint32_t ph = (it / ns) & 1;
+        if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1)) {
+          ok = false;
+          break;
+        }
+        uint8_t* ast = sm + s * L.stage_bytes;
+        const int k0 = kb * KB + 2 * lane;
+        unsigned long long v0[16], v1[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int rw = warp * 16 + i;
+          v0[i] = 0;
+          v1[i] = 0;
+          if (rw < rows) {
+            const double* xr = a.x + (ti.m0 + rw) * (long long)a.P;
+            if (k0 < a.P) v0[i] = (unsigned long long)__double_as_longlong(__ldg(xr + k0));
+            if (k0 + 1 < a.P)
+              v1[i] = (unsigned long long)__double_as_longlong(__ldg(xr + k0 + 1));
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int rw = warp * 16 + i;
+          if (k0 < a.P) mraw[i] = max(mraw[i], (long long)v0[i]);
+          if (k0 + 1 < a.P) mraw[i] = max(mraw[i], (long long)v1[i]);
+          const uint32_t packed =
+              bf16_of_f64_words((uint32_t)(v0[i] >> 32), (uint32_t)v0[i]) |
+              (bf16_of_f64_words((uint32_t)(v1[i] >> 32), (uint32_t)v1[i]) << 16);
+          *reinterpret_cast<uint32_t*>(ast + swz128(rw, lane >> 2) + (lane & 3) * 4) = packed;
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        mbar_arrive(&full_a[s]);
+      }
+      if (!ok) break;
+      // row maxima: lanes hold partial maxima of rows warp*16 + i
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        long long k = mraw[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) k = max(k, (long long)__shfl_xor_sync(0xffffffffu, k, o));
+        const int rw = warp * 16 + i;
+        if (k < 0 && rw < rows) {
+          // no non-negative value: the exact maximum on order-preserving keys
+          const double* xr = a.x + (ti.m0 + rw) * (long long)a.P;
+          long long kk = (long long)f64_key(0xFFF0000000000000ull);
+          for (int p = lane; p < a.P; p += 32)
+            kk = max(kk,
+                     (long long)f64_key((unsigned long long)__double_as_longlong(__ldg(xr + p))));
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1)
+            kk = max(kk, (long long)__shfl_xor_sync(0xffffffffu, kk, o));
+          k = (long long)f64_key((unsigned long long)kk);
+        }
+        if (lane == 0) rowmax[rw] = __longlong_as_double(k);
+      }
+      named_sync(1, NCONV * 32);
+      // ---- E1 epilogue: TMEM -> act(acc / s + b1) -> BF16 swizzled h tile ----
+      if (!mbar_wait(acc_full, tp)) {
         ok = false;
         break;
       }
-      uint8_t* ast = sm + s * L.stage_bytes;
-      const int k0 = kb * KB + 2 * lane;
-      unsigned long long v0[16], v1[16];
+      tc_fence_after();
+      {
+        const double srow = rowmax[r];
+        const float rs = (srow > 0.0 && isfinite(srow)) ? (float)(1.0 / srow) : 0.f;
+        const float* b1 = a.b1 + ti.g * a.b1_gs;
+        const int c_lo = half * (H / 2), c_hi = c_lo + H / 2;
+        for (int c = c_lo; c < c_hi; c += 32) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+          uint8_t* hb = sm + (c / KB) * A_STAGE;
+          const int ch0 = (c % KB) / 8;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int r = warp * 16 + i;
-        v0[i] = 0;
-        v1[i] = 0;
-        if (r < rows) {
-          const double* xr = a.x + (ti.m0 + r) * (long long)a.P;
-          if (k0 < a.P) v0[i] = (unsigned long long)__double_as_longlong(__ldg(xr + k0));
-          if (k0 + 1 < a.P) v1[i] = (unsigned long long)__double_as_longlong(__ldg(xr + k0 + 1));
+          for (int u = 0; u < 4; ++u) {
+            uint4 w;
+            w.x = pack_bf16(act_f(a.act, fmaf(v[8 * u + 0], rs, __ldg(b1 + c + 8 * u + 0))),
+                            act_f(a.act, fmaf(v[8 * u + 1], rs, __ldg(b1 + c + 8 * u + 1))));
+            w.y = pack_bf16(act_f(a.act, fmaf(v[8 * u + 2], rs, __ldg(b1 + c + 8 * u + 2))),
+                            act_f(a.act, fmaf(v[8 * u + 3], rs, __ldg(b1 + c + 8 * u + 3))));
+            w.z = pack_bf16(act_f(a.act, fmaf(v[8 * u + 4], rs, __ldg(b1 + c + 8 * u + 4))),
+                            act_f(a.act, fmaf(v[8 * u + 5], rs, __ldg(b1 + c + 8 * u + 5))));
+            w.w = pack_bf16(act_f(a.act, fmaf(v[8 * u + 6], rs, __ldg(b1 + c + 8 * u + 6))),
+                            act_f(a.act, fmaf(v[8 * u + 7], rs, __ldg(b1 + c + 8 * u + 7))));
+            *reinterpret_cast<uint4*>(hb + swz128(r, ch0 + u)) = w;
+          }
         }
-      }
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int r = warp * 16 + i;
-        if (k0 < a.P) mraw[i] = max(mraw[i], (long long)v0[i]);
-        if (k0 + 1 < a.P) mraw[i] = max(mraw[i], (long long)v1[i]);
-        const uint32_t packed =
-            bf16_of_f64_words((uint32_t)(v0[i] >> 32), (uint32_t)v0[i]) |
-            (bf16_of_f64_words((uint32_t)(v1[i] >> 32), (uint32_t)v1[i]) << 16);
-        *reinterpret_cast<uint32_t*>(ast + swz128(r, lane >> 2) + (lane & 3) * 4) = packed;
       }
       fence_proxy_async_smem();
-      mbar_arrive(&full_a[s]);
-    }
-    // row maxima: lanes hold partial maxima of rows warp*16 + i
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      long long k = mraw[i];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) k = max(k, (long long)__shfl_xor_sync(0xffffffffu, k, o));
-      const int r = warp * 16 + i;
-      if (k < 0 && r < rows) {
-        // no non-negative value: the exact maximum on order-preserving keys
-        const double* xr = a.x + (ti.m0 + r) * (long long)a.P;
-        long long kk = (long long)f64_key(0xFFF0000000000000ull);
-        for (int p = lane; p < a.P; p += 32)
-          kk = max(kk, (long long)f64_key((unsigned long long)__double_as_longlong(__ldg(xr + p))));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-          kk = max(kk, (long long)__shfl_xor_sync(0xffffffffu, kk, o));
-        k = (long long)f64_key((unsigned long long)kk);
-      }
-      if (lane == 0) rowmax[r] = __longlong_as_double(k);
-    }
-    named_sync(1, NCONV * 32);
-    // ---- E1 epilogue: TMEM -> act(acc / s + b1) -> BF16 swizzled h tile ----
-    const int q = warp & 3, half = warp >> 2;
-    const int r = q * 32 + lane;
-    if (ok && !mbar_wait(acc_full, 0)) {
-      ok = false;
-      fail();
-    }
-    if (ok) {
-      tc_fence_after();
-      const double srow = rowmax[r];
-      const float rs = (srow > 0.0 && isfinite(srow)) ? (float)(1.0 / srow) : 0.f;
-      const float* b1 = a.b1 + ti.g * a.b1_gs;
-      const int c_lo = half * (H / 2), c_hi = c_lo + H / 2;
-      for (int c = c_lo; c < c_hi; c += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
-        uint8_t* hb = sm + (c / KB) * A_STAGE;
-        const int ch0 = (c % KB) / 8;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          uint4 w;
-          w.x = pack_bf16(act_f(a.act, fmaf(v[8 * u + 0], rs, __ldg(b1 + c + 8 * u + 0))),
-                          act_f(a.act, fmaf(v[8 * u + 1], rs, __ldg(b1 + c + 8 * u + 1))));
-          w.y = pack_bf16(act_f(a.act, fmaf(v[8 * u + 2], rs, __ldg(b1 + c + 8 * u + 2))),
-                          act_f(a.act, fmaf(v[8 * u + 3], rs, __ldg(b1 + c + 8 * u + 3))));
-          w.z = pack_bf16(act_f(a.act, fmaf(v[8 * u + 4], rs, __ldg(b1 + c + 8 * u + 4))),
-                          act_f(a.act, fmaf(v[8 * u + 5], rs, __ldg(b1 + c + 8 * u + 5))));
-          w.w = pack_bf16(act_f(a.act, fmaf(v[8 * u + 6], rs, __ldg(b1 + c + 8 * u + 6))),
-                          act_f(a.act, fmaf(v[8 * u + 7], rs, __ldg(b1 + c + 8 * u + 7))));
-          *reinterpret_cast<uint4*>(hb + swz128(r, ch0 + u)) = w;
-        }
-      }
-    }
-    fence_proxy_async_smem();
-    tc_fence_before();
-    mbar_arrive(h1_full);
-    // ---- E2 epilogue: latent = acc + b2 (BF16), scale = s ----
-    if (warp < 4) {
-      if (ok && !mbar_wait(lat_full, 0)) {
+      tc_fence_before();
+      mbar_arrive(h1_full);
+      // ---- E2 epilogue: latent = acc + b2 (BF16), scale = s; every converter
+      // warp waits for the second MMA, whose operand h aliases the next
+      // tile's stages ----
+      if (!mbar_wait(lat_full, tp)) {
         ok = false;
-        fail();
+        break;
       }
-      if (ok && !*abort_flag) {
-        tc_fence_after();
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16), v);
-        if (r < rows) {
-          const float* b2 = a.b2 + ti.g * a.b2_gs;
-          uint32_t* dst = reinterpret_cast<uint32_t*>(a.latent + (ti.m0 + r) * a.L);
-          for (int l = 0; l < a.L; l += 2)
-            dst[l >> 1] = pack_bf16(v[l] + __ldg(b2 + l), v[l + 1] + __ldg(b2 + l + 1));
+      tc_fence_after();
+      if (warp < 4) {
+        if (!*abort_flag) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16), v);
+          if (r < rows) {
+            const float* b2 = a.b2 + ti.g * a.b2_gs;
+            uint32_t* dst = reinterpret_cast<uint32_t*>(a.latent + (ti.m0 + r) * a.L);
+            for (int l = 0; l < a.L; l += 2)
+              dst[l >> 1] = pack_bf16(v[l] + __ldg(b2 + l), v[l + 1] + __ldg(b2 + l + 1));
+          }
         }
+      } else {
+        const int rr = (warp - 4) * 32 + lane;
+        if (rr < rows) a.scale[ti.m0 + rr] = rowmax[rr];
       }
-    } else {
-      const int rr = (warp - 4) * 32 + lane;
-      if (rr < rows) a.scale[ti.m0 + rr] = rowmax[rr];
+      tc_fence_before();
+      ++iter;
     }
+    if (!ok) fail();
   }
   tc_fence_before();
   __syncthreads();
@@ -389,6 +431,7 @@ struct DecArgs {
   const __nv_bfloat16* latent;
   const double* scale;
   long long n;
+  long long ntiles;  // tiles to walk (grouped: an upper bound, spare tiles skipped)
   int P, H, L, act, G, ns;
   const long long* goff;
   const int* toff;
@@ -426,6 +469,13 @@ struct DecSmem {
   }
 };
 
+// Persistent like the encoder: one CTA per SM walks the tiles; the per-tile
+// barriers (d1_ops, d1_done, h_full) complete once per tile (parity i & 1 for
+// tile iteration i); the W4 stage ring and the double-buffered output
+// accumulators (tile counter J across all tiles of the CTA) continue from tile
+// to tile.  The D1 operands alias the W4 stages: the converters write the next
+// tile's only after draining this tile's last output tile (so every MMA of
+// this tile is complete), and the TMA warp streams W4 only after d1_done.
 __global__ void __launch_bounds__(NTHREADS, 1)
     dec_tc_kernel(const __grid_constant__ CUtensorMap mapW4, const DecArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -443,9 +493,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
-  TileInfo ti;
-  if (!tile_info(blockIdx.x, a.n, a.G, a.goff, a.toff, ti)) return;
-  const int rows = (int)min((long long)BM, ti.mend - ti.m0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int H = a.H, nk2 = H / KB, nh = (H + 255) / 256, hn = H < 256 ? H : 256;
   const int ntiles = (a.P + 255) / 256;
@@ -479,51 +526,68 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == WARP_TMA) {
     if (lane == 0) {
       prefetch_tmap(&mapW4);
-      // the stages alias the D1 operands: start after the D1 MMA has read them
-      if (!mbar_wait(d1_done, 0)) {
-        fail();
-      } else {
-        int it = 0;
-        for (int j = 0; j < ntiles && !*abort_flag; ++j)
+      int it = 0, iter = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < a.ntiles && ok && !*abort_flag; t += gridDim.x) {
+        TileInfo ti;
+        if (!tile_info((int)t, a.n, a.G, a.goff, a.toff, ti)) continue;
+        // the stages alias the D1 operands: start after the D1 MMA has read them
+        if (!mbar_wait(d1_done, iter & 1)) {
+          ok = false;
+          break;
+        }
+        for (int j = 0; j < ntiles && ok; ++j)
           for (int k2 = 0; k2 < nk2; ++k2, ++it) {
             const int s = it % ns;
             const uint32_t ph = (it / ns) & 1;
-            if (!mbar_wait(&empty[s], ph ^ 1)) {
-              fail();
-              j = ntiles;
+            if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1)) {
+              ok = false;
               break;
             }
             mbar_arrive_expect_tx(&full_b[s], 256 * 128);
             tma_load_3d(sm + L.stages + s * 256 * 128, &mapW4, &full_b[s], k2 * KB, j * 256,
                         ti.g);
           }
+        ++iter;
       }
+      if (!ok) fail();
     }
     __syncwarp();
   } else if (warp == WARP_MMA) {
     if (lane == 0) {
-      bool ok = mbar_wait(d1_ops, 0);
-      if (ok) {
+      const uint32_t id1 = idesc_bf16(BM, hn);
+      const uint32_t id2 = idesc_bf16(BM, 256);
+      int it = 0, iter = 0, J = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+        TileInfo ti;
+        if (!tile_info((int)t, a.n, a.G, a.goff, a.toff, ti)) continue;
+        const uint32_t tp = iter & 1;
+        if (!mbar_wait(d1_ops, tp)) {
+          ok = false;
+          mma_commit(d1_done);
+          break;
+        }
         tc_fence_after();
-        const uint32_t id1 = idesc_bf16(BM, hn);
-        const uint32_t abase = smem_u32(sm + L.d1a), bbase = smem_u32(sm + L.d1b);
+        {
+          const uint32_t abase = smem_u32(sm + L.d1a), bbase = smem_u32(sm + L.d1b);
 #pragma unroll
-        for (int kk = 0; kk < KB / 16; ++kk)
-          for (int j = 0; j < nh; ++j)
-            mma_bf16(tmem + j * 256, desc_k128(abase + kk * 32),
-                     desc_k128(bbase + j * 256 * 128 + kk * 32), id1, kk != 0);
-      }
-      mma_commit(d1_done);
-      if (ok) ok = mbar_wait(h_full, 0);
-      if (ok) {
+          for (int kk = 0; kk < KB / 16; ++kk)
+            for (int j = 0; j < nh; ++j)
+              mma_bf16(tmem + j * 256, desc_k128(abase + kk * 32),
+                       desc_k128(bbase + j * 256 * 128 + kk * 32), id1, kk != 0);
+        }
+        mma_commit(d1_done);
+        if (!mbar_wait(h_full, tp)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
-        const uint32_t id2 = idesc_bf16(BM, 256);
         const uint32_t hbase = smem_u32(sm + L.h);
-        int it = 0;
-        for (int j = 0; j < ntiles && ok; ++j) {
-          const int buf = j & 1;
-          // wait until the epilogue has drained this accumulator (tile j - 2)
-          if (j >= 2 && !mbar_wait(&acc_empty[buf], ((j >> 1) - 1) & 1)) {
+        for (int j = 0; j < ntiles && ok; ++j, ++J) {
+          const int buf = J & 1;
+          // wait until the epilogue has drained this accumulator (tile J - 2)
+          if (J >= 2 && !mbar_wait(&acc_empty[buf], ((J >> 1) - 1) & 1)) {
             ok = false;
             break;
           }
@@ -545,123 +609,131 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           mma_commit(&acc_full[buf]);
         }
+        ++iter;
       }
       if (!ok) fail();
     }
     __syncwarp();
   } else {
-    const int t = threadIdx.x;
-    bool ok = true;
-    // ---- D1 operands: latent tile [128][64] and W3 [H][64] (K zero-padded) ----
-    {
-      const __nv_bfloat16* W3 = a.W3 + ti.g * a.w3_gs;
-      // latent: 128 rows x 8 chunks of 16 B; chunk c holds k = 8c..8c+7
-      for (int idx = t; idx < BM * 8; idx += NCONV * 32) {
-        const int r = idx >> 3, c = idx & 7;
-        uint4 w = make_uint4(0, 0, 0, 0);
-        if (r < rows && c * 8 < a.L)
-          w = *reinterpret_cast<const uint4*>(a.latent + (ti.m0 + r) * a.L + c * 8);
-        *reinterpret_cast<uint4*>(sm + L.d1a + swz128(r, c)) = w;
-      }
-      for (int idx = t; idx < H * 8; idx += NCONV * 32) {
-        const int r = idx >> 3, c = idx & 7;
-        uint4 w = make_uint4(0, 0, 0, 0);
-        if (c * 8 < a.L) w = *reinterpret_cast<const uint4*>(W3 + (long long)r * a.L + c * 8);
-        // rows beyond 256 go to the second 256-row block (row r of block r / 256)
-        *reinterpret_cast<uint4*>(sm + L.d1b + (r >> 8) * 256 * 128 + swz128(r & 255, c)) = w;
-      }
-      fence_proxy_async_smem();
-      mbar_arrive(d1_ops);
-    }
-    // ---- D1 epilogue: h = act(acc + b3) -> BF16 swizzled h tile ----
+    const int t_ = threadIdx.x;
     const int q = warp & 3, half = warp >> 2;
     const int r = q * 32 + lane;
-    if (!mbar_wait(d1_done, 0)) {
-      ok = false;
-      fail();
-    }
-    if (ok) {
-      tc_fence_after();
-      const float* b3 = a.b3 + ti.g * a.b3_gs;
-      const int c_lo = half * (H / 2), c_hi = c_lo + H / 2;
-      for (int c = c_lo; c < c_hi; c += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
-        uint8_t* hb = sm + L.h + (c / KB) * A_STAGE;
-        const int ch0 = (c % KB) / 8;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          uint4 w;
-          w.x = pack_bf16(act_f(a.act, v[8 * u + 0] + __ldg(b3 + c + 8 * u + 0)),
-                          act_f(a.act, v[8 * u + 1] + __ldg(b3 + c + 8 * u + 1)));
-          w.y = pack_bf16(act_f(a.act, v[8 * u + 2] + __ldg(b3 + c + 8 * u + 2)),
-                          act_f(a.act, v[8 * u + 3] + __ldg(b3 + c + 8 * u + 3)));
-          w.z = pack_bf16(act_f(a.act, v[8 * u + 4] + __ldg(b3 + c + 8 * u + 4)),
-                          act_f(a.act, v[8 * u + 5] + __ldg(b3 + c + 8 * u + 5)));
-          w.w = pack_bf16(act_f(a.act, v[8 * u + 6] + __ldg(b3 + c + 8 * u + 6)),
-                          act_f(a.act, v[8 * u + 7] + __ldg(b3 + c + 8 * u + 7)));
-          *reinterpret_cast<uint4*>(hb + swz128(r, ch0 + u)) = w;
-        }
-      }
-    }
-    fence_proxy_async_smem();
-    tc_fence_before();
-    mbar_arrive(h_full);
-    // ---- D2 epilogue per 256-column tile: xhat = s (acc + b4) ----
-    // each thread holds one row; the values go through a per-warp staging
-    // block so that every store instruction writes whole rows segments
-    const float* b4 = a.b4 + ti.g * a.b4_gs;
-    const float rs = r < rows ? (float)a.scale[ti.m0 + r] : 0.f;
     const int sw = a.sw;
     float* stg = reinterpret_cast<float*>(sm + L.stg) + warp * 32 * (sw + 1);
     const int rpi = 32 / sw;                    // rows per store instruction
     const int sub_r = lane / sw, sub_c = lane % sw;
-    for (int j = 0; j < ntiles; ++j) {
-      const int buf = j & 1;
-      if (ok && (*abort_flag || !mbar_wait(&acc_full[buf], (j >> 1) & 1))) {
-        ok = false;
-        fail();
+    int iter = 0, J = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+      TileInfo ti;
+      if (!tile_info((int)t, a.n, a.G, a.goff, a.toff, ti)) continue;
+      const int rows = (int)min((long long)BM, ti.mend - ti.m0);
+      const uint32_t tp = iter & 1;
+      // ---- D1 operands: latent tile [128][64] and W3 [H][64] (K zero-padded) ----
+      {
+        const __nv_bfloat16* W3 = a.W3 + ti.g * a.w3_gs;
+        // latent: 128 rows x 8 chunks of 16 B; chunk c holds k = 8c..8c+7
+        for (int idx = t_; idx < BM * 8; idx += NCONV * 32) {
+          const int rw = idx >> 3, c = idx & 7;
+          uint4 w = make_uint4(0, 0, 0, 0);
+          if (rw < rows && c * 8 < a.L)
+            w = *reinterpret_cast<const uint4*>(a.latent + (ti.m0 + rw) * a.L + c * 8);
+          *reinterpret_cast<uint4*>(sm + L.d1a + swz128(rw, c)) = w;
+        }
+        for (int idx = t_; idx < H * 8; idx += NCONV * 32) {
+          const int rw = idx >> 3, c = idx & 7;
+          uint4 w = make_uint4(0, 0, 0, 0);
+          if (c * 8 < a.L) w = *reinterpret_cast<const uint4*>(W3 + (long long)rw * a.L + c * 8);
+          // rows beyond 256 go to the second 256-row block (row r of block r / 256)
+          *reinterpret_cast<uint4*>(sm + L.d1b + (rw >> 8) * 256 * 128 + swz128(rw & 255, c)) = w;
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        mbar_arrive(d1_ops);
       }
-      if (ok) {
-        tc_fence_after();
-#pragma unroll 1
-        for (int cc = 0; cc < 128; cc += 32) {
-          const int col = half * 128 + cc;
+      // ---- D1 epilogue: h = act(acc + b3) -> BF16 swizzled h tile ----
+      if (!mbar_wait(d1_done, tp)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      {
+        const float* b3 = a.b3 + ti.g * a.b3_gs;
+        const int c_lo = half * (H / 2), c_hi = c_lo + H / 2;
+        for (int c = c_lo; c < c_hi; c += 32) {
           float v[32];
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + col), v);
-          const int p0 = j * 256 + col;
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+          uint8_t* hb = sm + L.h + (c / KB) * A_STAGE;
+          const int ch0 = (c % KB) / 8;
 #pragma unroll
-          for (int h0 = 0; h0 < 32; h0 += 16) {
-            if (sw == 16 || h0 == 0) {
-              __syncwarp();
-              const int nc = sw == 16 ? 16 : 32;
+          for (int u = 0; u < 4; ++u) {
+            uint4 w;
+            w.x = pack_bf16(act_f(a.act, v[8 * u + 0] + __ldg(b3 + c + 8 * u + 0)),
+                            act_f(a.act, v[8 * u + 1] + __ldg(b3 + c + 8 * u + 1)));
+            w.y = pack_bf16(act_f(a.act, v[8 * u + 2] + __ldg(b3 + c + 8 * u + 2)),
+                            act_f(a.act, v[8 * u + 3] + __ldg(b3 + c + 8 * u + 3)));
+            w.z = pack_bf16(act_f(a.act, v[8 * u + 4] + __ldg(b3 + c + 8 * u + 4)),
+                            act_f(a.act, v[8 * u + 5] + __ldg(b3 + c + 8 * u + 5)));
+            w.w = pack_bf16(act_f(a.act, v[8 * u + 6] + __ldg(b3 + c + 8 * u + 6)),
+                            act_f(a.act, v[8 * u + 7] + __ldg(b3 + c + 8 * u + 7)));
+            *reinterpret_cast<uint4*>(hb + swz128(r, ch0 + u)) = w;
+          }
+        }
+      }
+      fence_proxy_async_smem();
+      tc_fence_before();
+      mbar_arrive(h_full);
+      // ---- D2 epilogue per 256-column tile: xhat = s (acc + b4) ----
+      // each thread holds one row; the values go through a per-warp staging
+      // block so that every store instruction writes whole rows segments
+      const float* b4 = a.b4 + ti.g * a.b4_gs;
+      const float rs = r < rows ? (float)a.scale[ti.m0 + r] : 0.f;
+      for (int j = 0; j < ntiles; ++j, ++J) {
+        const int buf = J & 1;
+        if (ok && (*abort_flag || !mbar_wait(&acc_full[buf], (J >> 1) & 1))) ok = false;
+        if (ok) {
+          tc_fence_after();
+#pragma unroll 1
+          for (int cc = 0; cc < 128; cc += 32) {
+            const int col = half * 128 + cc;
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + col), v);
+            const int p0 = j * 256 + col;
 #pragma unroll
-              for (int i = 0; i < 16; ++i) {
-                const int pc = p0 + h0 + i;
-                stg[lane * (sw + 1) + i] = rs * (v[h0 + i] + (pc < a.P ? __ldg(b4 + pc) : 0.f));
-              }
-              if (nc == 32) {
+            for (int h0 = 0; h0 < 32; h0 += 16) {
+              if (sw == 16 || h0 == 0) {
+                __syncwarp();
+                const int nc = sw == 16 ? 16 : 32;
 #pragma unroll
-                for (int i = 16; i < 32; ++i) {
-                  const int pc = p0 + i;
-                  stg[lane * (sw + 1) + i] = rs * (v[i] + (pc < a.P ? __ldg(b4 + pc) : 0.f));
+                for (int i = 0; i < 16; ++i) {
+                  const int pc = p0 + h0 + i;
+                  stg[lane * (sw + 1) + i] = rs * (v[h0 + i] + (pc < a.P ? __ldg(b4 + pc) : 0.f));
                 }
-              }
-              __syncwarp();
-              // rows q*32 + rr .. of this warp, columns p0 + h0 + sub_c
-              const int pcol = p0 + (sw == 16 ? h0 : 0) + sub_c;
-              for (int rr = sub_r; rr < 32; rr += rpi) {
-                const int row = q * 32 + rr;
-                if (row < rows && pcol < a.P)
-                  a.xhat[(ti.m0 + row) * a.ld + pcol] = stg[rr * (sw + 1) + sub_c];
+                if (nc == 32) {
+#pragma unroll
+                  for (int i = 16; i < 32; ++i) {
+                    const int pc = p0 + i;
+                    stg[lane * (sw + 1) + i] = rs * (v[i] + (pc < a.P ? __ldg(b4 + pc) : 0.f));
+                  }
+                }
+                __syncwarp();
+                // rows q*32 + rr .. of this warp, columns p0 + h0 + sub_c
+                const int pcol = p0 + (sw == 16 ? h0 : 0) + sub_c;
+                for (int rr = sub_r; rr < 32; rr += rpi) {
+                  const int row = q * 32 + rr;
+                  if (row < rows && pcol < a.P)
+                    a.xhat[(ti.m0 + row) * a.ld + pcol] = stg[rr * (sw + 1) + sub_c];
+                }
               }
             }
           }
         }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[buf]);
       }
-      tc_fence_before();
-      mbar_arrive(&acc_empty[buf]);
+      ++iter;
     }
+    if (!ok) fail();
   }
   tc_fence_before();
   __syncthreads();
@@ -715,6 +787,14 @@ bool tc_shape_ok(int H, int L) {
   return H % 64 == 0 && H >= 64 && H <= 512 && (L == 16 || L == 32);
 }
 
+// one CTA per SM (each takes the whole shared memory), at most one per tile
+unsigned persistent_grid(long long ntiles) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return (unsigned)(ntiles < sms ? (ntiles > 0 ? ntiles : 1) : sms);
+}
+
 int run_encode_tc(aeqc_model* m, const double* x, long long n, const long long* group_off,
                   const int* tile_off, int G, void* latent, double* scale, int* err,
                   cudaStream_t s) {
@@ -754,8 +834,8 @@ int run_encode_tc(aeqc_model* m, const double* x, long long n, const long long* 
     const int rc = raise_smem_limit((const void*)enc_tc_kernel, 227 * 1024);
     if (rc) return rc;
   }
-  const long long tiles = G > 1 ? (n + BM - 1) / BM + G : (n + BM - 1) / BM;
-  enc_tc_kernel<<<(unsigned)tiles, NTHREADS, smem, s>>>(mW1, mW2, a);
+  a.ntiles = G > 1 ? (n + BM - 1) / BM + G : (n + BM - 1) / BM;
+  enc_tc_kernel<<<persistent_grid(a.ntiles), NTHREADS, smem, s>>>(mW1, mW2, a);
   return check_launch("enc_tc_kernel");
 }
 
@@ -801,8 +881,8 @@ int run_decode_tc(aeqc_model* m, const void* latent, const double* scale, long l
     const int rc = raise_smem_limit((const void*)dec_tc_kernel, 227 * 1024);
     if (rc) return rc;
   }
-  const long long tiles = G > 1 ? (n + BM - 1) / BM + G : (n + BM - 1) / BM;
-  dec_tc_kernel<<<(unsigned)tiles, NTHREADS, smem, s>>>(mW4, a);
+  a.ntiles = G > 1 ? (n + BM - 1) / BM + G : (n + BM - 1) / BM;
+  dec_tc_kernel<<<persistent_grid(a.ntiles), NTHREADS, smem, s>>>(mW4, a);
   return check_launch("dec_tc_kernel");
 }
 

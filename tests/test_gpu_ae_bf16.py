@@ -150,3 +150,46 @@ def emulate_decoder(p, z, s, act, tied):
 def test_bf16_shapes_outside_the_tensor_core_path_are_refused(aq):
     with pytest.raises(RuntimeError, match="BF16 models need"):
         aq.Model(1521, 96, 32, dtype=aq.DTYPE_BF16)
+
+
+@pytest.mark.parametrize("H,L,tied,sizes", [
+    (512, 32, True, [152 * 128 * 3 + 77]),          # three or four tiles per CTA
+    (256, 32, True, [9000, 0, 31000, 1, 18000]),    # tiles of several groups per CTA
+])
+def test_bf16_persistent_tiles(aq, H, L, tied, sizes):
+    """The persistent encoder and decoder (one CTA per SM walking the tiles):
+    batches of several tiles per CTA, ungrouped and grouped, against the
+    BF16 emulation on sampled rows of every group (first, last and evenly
+    spaced rows, so every CTA's later tiles are among them)."""
+    P = 1521
+    G = len(sizes)
+    m = aq.Model(P, H, L, tied=tied, act=0, dtype=aq.DTYPE_BF16, n_groups=G)
+    prms = []
+    for g in range(G):
+        d = rand_params(P, H, L, tied, 90 + g)
+        m.set_group(g, d)
+        prms.append(d)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    xd = synth.histograms_torch(n, synth.config_seed(2) + H, DEV)
+    goff = dev(off) if G > 1 else None
+    z, s = aq.ae_encode(m, xd, group_offsets=goff)
+    xh = aq.ae_decode(m, z, s, group_offsets=goff)
+    torch.cuda.synchronize()
+    for g in range(G):
+        if sizes[g] == 0:
+            continue
+        rows = np.unique(np.concatenate([np.linspace(off[g], off[g + 1] - 1, 97),
+                                         [off[g], off[g + 1] - 1]]).astype(np.int64))
+        idx = torch.as_tensor(rows, device=DEV)
+        x = xd[idx].cpu().numpy()
+        zg = z[idx].float().cpu().numpy().astype(np.float64)
+        sg = s[idx].cpu().numpy()
+        xg = xh[idx].cpu().numpy()[:, :P].astype(np.float64)
+        assert np.array_equal(sg, x.max(axis=1))
+        ze, _, _ = emulate(prms[g], x, 0, tied)
+        zsc = np.abs(ze).max(axis=1, keepdims=True) + 1e-30
+        assert np.all(np.abs(zg - ze) <= 2.0 ** -7 * np.abs(ze) + 1e-3 * zsc), g
+        _, xe, _ = emulate_decoder(prms[g], zg, sg, 0, tied)
+        xsc = np.abs(xe).max(axis=1, keepdims=True) + 1e-30
+        assert np.all(np.abs(xg - xe) <= 2e-3 * xsc), g

@@ -991,6 +991,39 @@ __device__ __noinline__ void write_features(const FusedArgs& a, long long b, flo
   if (lane < 4) fr[z.L + lane] = d;
 }
 
+// Verbatim storage after a certain end-to-end violation at both levels (the
+// oracle's result for it: every code escapes, the raw values go to the
+// outlier list, lambda = 0, f = x); out of line, since it is rare.
+__device__ __noinline__ void write_verbatim(const FusedArgs& a, long long b, double s, unsigned st,
+                                            int total_it, float d0, float d1, float d2,
+                                            float d3, int lane) {
+  const int P = a.grid.P;
+  int16_t* cb = a.codes + b * (long long)P;
+  const double* xb = a.x + b * (long long)P;
+  for (int p = lane; p < P; p += 32) cb[p] = (int16_t)AEQC_CODE_ESCAPE;
+  if (a.f_out) {
+    double* fb = a.f_out + b * (long long)P;
+    for (int p = lane; p < P; p += 32) fb[p] = __ldg(xb + p);
+  }
+  __syncwarp();
+  if (a.out.count && append_outliers(a.out, cb, xb, P, a.row0 + b, lane))
+    st |= AEQC_ST_OUTLIER_OVERFLOW;
+  if (a.features) {
+    const LatentK& z = a.latent;
+    float* fr = a.features + b * (long long)(z.L + 4);
+    for (int l = lane; l < z.L; l += 32) fr[l] = load_latent(z, b, l);
+    const float d = lane == 0 ? d0 : (lane == 1 ? d1 : (lane == 2 ? d2 : d3));
+    if (lane < 4) fr[z.L + lane] = d;
+  }
+  if (lane < 4) a.lambda[b * 4 + lane] = 0.0;
+  if (lane == 0) {
+    a.scale[b] = s;
+    a.iters[b] = (uint8_t)(total_it > 255 ? 255 : total_it);
+    a.status[b] = (uint16_t)st;
+  }
+  __syncwarp();
+}
+
 __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int lane) {
   const GridK& g = a.grid;
   const ParamsK& pr = a.prm;
@@ -1033,7 +1066,7 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
   df lam[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   int total_it = 0;
   float dfeat[4] = {0.f, 0.f, 0.f, 0.f};
-  bool done = false;
+  bool done = false, verbatim = false;
   const float s_f = float_of_bits(umax);  // s to 24 bits (margins only)
   // not unrolled: one copy of the quantizer and of the Newton loop serves both
   // levels (alpha, then alpha / 4)
@@ -1116,7 +1149,18 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
 #pragma unroll
     for (int k = 0; k < 4; ++k) qoi_ok = qoi_ok && ns.gres[k] <= pr.qoi_check_f;
     if (!ns.check_viol && qoi_ok) done = true;
-    else if (level == 1) defer = true;  // verbatim after the retry: the FP64 kernel stores it
+    else if (level == 1) {
+      // a certain pointwise violation at alpha / 4 too: verbatim, as the
+      // oracle stores it; a moment check that fails only by its error bound
+      // goes to the FP64 kernel
+      if (ns.check_viol) verbatim = true;
+      else defer = true;
+    }
+  }
+  if (verbatim && !defer) {
+    write_verbatim(a, b, s, (st & AEQC_ST_WARM_REJECTED) | AEQC_ST_VERBATIM | AEQC_ST_ALPHA_RETRY,
+                   total_it, dfeat[0], dfeat[1], dfeat[2], dfeat[3], lane);
+    return;
   }
   if (defer || !done) {
     if (lane == 0) {

@@ -435,3 +435,23 @@ def test_fast_kernel_converged_means_residual_below_tol(aq, grids, tau, pattern)
     assert np.mean((st & oracle.CONVERGED) != 0) >= 0.9
     if (tau, pattern) == (3e-3, "quad"):
         assert reach_t > 0.02 and reach_h > 3e-6, (reach_t, reach_h)
+
+
+@pytest.mark.parametrize("kernel", ["fast", "fp64"])
+def test_verbatim_after_the_retry_matches_oracle(aq, grids, kernel):
+    """Heavy-tailed histograms whose corrected output breaks the pointwise
+    bound at alpha and again at alpha / 4 are stored verbatim (status
+    VERBATIM | ALPHA_RETRY, every code an escape, f = x, lambda = 0): the fast
+    kernel stores them itself when the violation is certain, as the oracle
+    and the FP64 kernel do."""
+    _, og = grids
+    x = synth.histograms(400, synth.config_seed(0) + 61, k_max=4, heavy_frac=1.0)
+    xh = synth.stand_in_xhat(x, 61)
+    k = aq.KERNEL_FP64 if kernel == "fp64" else aq.KERNEL_FAST
+    out, ref = check_batch(aq, og, x, xh, 1e-4, k, n_expect_conv=0.9)
+    st = out.status.cpu().numpy()
+    vb = st == (oracle.VERBATIM | oracle.ALPHA_RETRY)
+    assert vb.sum() >= 5
+    assert np.all(out.lam.cpu().numpy()[vb] == 0.0)
+    assert np.array_equal(out.f.cpu().numpy()[vb], x[vb])
+    assert np.all(out.codes.cpu().numpy()[vb] == oracle.ESCAPE)

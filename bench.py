@@ -292,9 +292,10 @@ def build_workload(cfg, n, rank, device, aq, synth, train_steps=None):
 
 
 # DRAM bytes (read + write) per histogram of the correction kernel, from one
-# ncu capture of 65,536 histograms per form (the traffic grows in proportion
-# to the count); None where the kernel changed after the capture
-TRAFFIC_PER_HIST = {"optimized": 21496, "plain": 21270}
+# ncu capture of 65,536 histograms of the precision workload per form (the
+# traffic grows in proportion to the count); None where the kernel changed
+# after the capture
+TRAFFIC_PER_HIST = {"optimized": 21471, "plain": 21270}
 
 
 def algorithmic_bytes_fused(P=1521):

@@ -151,7 +151,7 @@ int aeqc_model_destroy(aeqc_model* m);
 /* Launch choices of a model's kernels (no effect on results, only on speed).
  * 0 in a field selects the built-in default.
  *   enc_stages, dec_stages  pipeline depth of the BF16 tensor-core encoder /
- *                           decoder (2..6 / 2..4; reduced to what fits in
+ *                           decoder (2..6 / 2..16; reduced to what fits in
  *                           shared memory)
  *   qc_ctas_per_sm          CTAs of the correction kernel per SM (1..4) in
  *                           compress_batch and compress_batch_host */

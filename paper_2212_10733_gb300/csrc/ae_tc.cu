@@ -12,9 +12,12 @@
 // neither h nor the BF16 copy of x touches HBM.
 //
 // Decoder (one kernel): h = act(z W3 + b3) then xhat = s (h W4' + b4'), with
-// W4' = sigma W4 and b4' = sigma b4 + mu; h stays in shared memory and the
-// output tiles of 256 columns are double-buffered in tensor memory so that
-// the FP32 stores of one tile overlap the MMAs of the next.
+// W4' = sigma W4 and b4' = sigma b4 + mu; h goes from the first layer's
+// accumulator back into tensor memory as packed BF16 and is the A operand of
+// the second layer, W4 streams through a shared-memory ring, and the output
+// tiles of 128 columns are double-buffered in tensor memory; their FP32 rows
+// leave through TMA stores, so that the stores of one tile overlap the MMAs of
+// the next.
 #include <cuda_bf16.h>
 #include <string.h>
 
@@ -443,59 +446,93 @@ struct DecArgs {
   long long b4_gs;
   float* xhat;
   long long ld;
-  int sw;  // staging width (32 or 16 columns)
+  int tma;  // 1: full tiles of xhat are written by TMA stores through mapX
   int* err;
 };
 
+// Decoder layout: D1 operands (latent tile and one chunk of W3) and the W4
+// stage ring in shared memory; h lives in tensor memory (the A operand of
+// the second layer).  offsets from a 1024-byte aligned base
+constexpr int DNT = 128;                    // output columns per accumulator use
+constexpr uint32_t D_STAGE = DNT * 128;     // one W4 stage: 128 rows x 64 bf16 of K
+constexpr uint32_t TM_ACC = 256;            // TMEM column of the first accumulator
+
+constexpr uint32_t D_OUT = 32 * 128;        // one output box: 32 rows x 32 FP32
+
 struct DecSmem {
-  uint32_t h, stages, d1a, d1b, stg, bars, total;
-  // sw: columns of the per-warp staging block (32 rows x sw, pitch sw + 1)
-  // through which the epilogue turns row-per-thread values into row-contiguous
-  // coalesced stores
-  __host__ __device__ DecSmem(int H, int ns, int sw) {
-    h = 0;  // BF16 h tile: (H / 64) blocks of 128 rows x 128 B
-    uint32_t o = (uint32_t)BM * H * 2;
-    stages = o;  // B stages: 256 rows x 128 B each; D1 operands alias them
-    const uint32_t st = (uint32_t)ns * 256 * 128;
-    d1a = stages;                    // latent tile, K padded to 64: 16 KB
-    d1b = stages + A_STAGE;          // W3 tile [H rows][64]: H * 128 B
-    const uint32_t d1 = A_STAGE + (uint32_t)H * 128;
-    o += st > d1 ? st : d1;
+  uint32_t d1a, d1b, stages, stg, bars, total;
+  __host__ __device__ explicit DecSmem(int ns) {
+    d1a = 0;                 // latent tile: 128 rows x 128 B (K padded to 64)
+    d1b = A_STAGE;           // W3 chunk: up to 128 rows x 128 B
+    stages = 2 * A_STAGE;    // W4 ring
+    uint32_t o = stages + (uint32_t)ns * D_STAGE;
+    // per epilogue warp two output boxes in the 128-byte-swizzled layout the
+    // TMA store reads (the rows of a partial tile reuse them as a 32 x 33
+    // transposition block)
     stg = o;
-    o += NCONV * 32 * (sw + 1) * 4;
+    o += NCONV * 2 * D_OUT;
     bars = o;
     o += 8 * (2 * ns + 8) + 16;
     total = o;
   }
 };
 
-// Persistent like the encoder: one CTA per SM walks the tiles; the per-tile
-// barriers (d1_ops, d1_done, h_full) complete once per tile (parity i & 1 for
-// tile iteration i); the W4 stage ring and the double-buffered output
-// accumulators (tile counter J across all tiles of the CTA) continue from tile
-// to tile.  The D1 operands alias the W4 stages: the converters write the next
-// tile's only after draining this tile's last output tile (so every MMA of
-// this tile is complete), and the TMA warp streams W4 only after d1_done.
+// h (packed BF16) from a tensor-memory accumulator: 32 columns of one row
+// per thread, b3 added, activation, two values per 32-bit TMEM column
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// D[tmem] (+)= A[tmem] * B[smem]^T: A in tensor memory, one row per lane, two
+// bf16 of K per 32-bit column (even k in the low half), 8 columns per K = 16
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Persistent like the encoder: one CTA per SM walks the tiles.  Per tile the
+// accumulator is used H / 128 times for the first layer (chunks of 128 hidden
+// units, their epilogue writing packed BF16 h into tensor memory) and then
+// once per 128 output columns for the second (A = h from tensor memory, B =
+// W4 from the ring); the uses alternate between two TMEM accumulators, with
+// acc_full / acc_empty counted over all uses of the CTA.  The TMA warp streams
+// W4 independently of the first layer (separate shared memory), so it runs
+// ahead into the next tile as far as the ring allows.
 __global__ void __launch_bounds__(NTHREADS, 1)
-    dec_tc_kernel(const __grid_constant__ CUtensorMap mapW4, const DecArgs a) {
+    dec_tc_kernel(const __grid_constant__ CUtensorMap mapW4, const __grid_constant__ CUtensorMap mapX,
+                  const DecArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                            ~uintptr_t(1023));
-  const DecSmem L(a.H, a.ns, a.sw);
+  const DecSmem L(a.ns);
   const int ns = a.ns;
   uint64_t* full_b = reinterpret_cast<uint64_t*>(sm + L.bars);
   uint64_t* empty = full_b + ns;
-  uint64_t* d1_ops = empty + ns;    // D1 operands written (converter warps)
-  uint64_t* d1_done = d1_ops + 1;   // D1 MMA complete
-  uint64_t* h_full = d1_done + 1;   // BF16 h tile written
-  uint64_t* acc_full = h_full + 1;  // [2]
+  uint64_t* d1_ops = empty + ns;       // latent + W3 chunk written (converter warps)
+  uint64_t* h_full = d1_ops + 1;       // every chunk of h stored in TMEM
+  uint64_t* acc_full = h_full + 1;     // [2]
   uint64_t* acc_empty = acc_full + 2;  // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int H = a.H, nk2 = H / KB, nh = (H + 255) / 256, hn = H < 256 ? H : 256;
-  const int ntiles = (a.P + 255) / 256;
+  const int H = a.H, nk2 = H / KB, nchunk = (H + DNT - 1) / DNT;
+  const int ntiles = (a.P + DNT - 1) / DNT;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
@@ -503,7 +540,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&empty[s], 1);
     }
     mbar_init(d1_ops, NCONV * 32);
-    mbar_init(d1_done, 1);
     mbar_init(h_full, NCONV * 32);
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
@@ -526,16 +562,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == WARP_TMA) {
     if (lane == 0) {
       prefetch_tmap(&mapW4);
-      int it = 0, iter = 0;
+      if (a.tma) prefetch_tmap(&mapX);
+      int it = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < a.ntiles && ok && !*abort_flag; t += gridDim.x) {
         TileInfo ti;
         if (!tile_info((int)t, a.n, a.G, a.goff, a.toff, ti)) continue;
-        // the stages alias the D1 operands: start after the D1 MMA has read them
-        if (!mbar_wait(d1_done, iter & 1)) {
-          ok = false;
-          break;
-        }
         for (int j = 0; j < ntiles && ok; ++j)
           for (int k2 = 0; k2 < nk2; ++k2, ++it) {
             const int s = it % ns;
@@ -544,49 +576,47 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               ok = false;
               break;
             }
-            mbar_arrive_expect_tx(&full_b[s], 256 * 128);
-            tma_load_3d(sm + L.stages + s * 256 * 128, &mapW4, &full_b[s], k2 * KB, j * 256,
-                        ti.g);
+            mbar_arrive_expect_tx(&full_b[s], D_STAGE);
+            tma_load_3d(sm + L.stages + s * D_STAGE, &mapW4, &full_b[s], k2 * KB, j * DNT, ti.g);
           }
-        ++iter;
       }
       if (!ok) fail();
     }
     __syncwarp();
   } else if (warp == WARP_MMA) {
     if (lane == 0) {
-      const uint32_t id1 = idesc_bf16(BM, hn);
-      const uint32_t id2 = idesc_bf16(BM, 256);
-      int it = 0, iter = 0, J = 0;
+      const uint32_t id2 = idesc_bf16(BM, DNT);
+      int it = 0, iter = 0, J = 0, nd1 = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         TileInfo ti;
         if (!tile_info((int)t, a.n, a.G, a.goff, a.toff, ti)) continue;
-        const uint32_t tp = iter & 1;
-        if (!mbar_wait(d1_ops, tp)) {
-          ok = false;
-          mma_commit(d1_done);
-          break;
-        }
-        tc_fence_after();
-        {
+        // first layer, chunk by chunk: acc = latent W3[chunk]^T
+        for (int c = 0; c < nchunk && ok; ++c, ++J, ++nd1) {
+          const int buf = J & 1, cw = min(DNT, H - c * DNT);
+          if (!mbar_wait(d1_ops, nd1 & 1) ||
+              (J >= 2 && !mbar_wait(&acc_empty[buf], ((J >> 1) - 1) & 1))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
           const uint32_t abase = smem_u32(sm + L.d1a), bbase = smem_u32(sm + L.d1b);
+          const uint32_t id1 = idesc_bf16(BM, cw);
 #pragma unroll
           for (int kk = 0; kk < KB / 16; ++kk)
-            for (int j = 0; j < nh; ++j)
-              mma_bf16(tmem + j * 256, desc_k128(abase + kk * 32),
-                       desc_k128(bbase + j * 256 * 128 + kk * 32), id1, kk != 0);
+            mma_bf16(tmem + TM_ACC + buf * DNT, desc_k128(abase + kk * 32),
+                     desc_k128(bbase + kk * 32), id1, kk != 0);
+          mma_commit(&acc_full[buf]);
         }
-        mma_commit(d1_done);
-        if (!mbar_wait(h_full, tp)) {
+        if (!ok) break;
+        // second layer: 128 output columns per accumulator use, A = h (TMEM)
+        if (!mbar_wait(h_full, iter & 1)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t hbase = smem_u32(sm + L.h);
         for (int j = 0; j < ntiles && ok; ++j, ++J) {
           const int buf = J & 1;
-          // wait until the epilogue has drained this accumulator (tile J - 2)
           if (J >= 2 && !mbar_wait(&acc_empty[buf], ((J >> 1) - 1) & 1)) {
             ok = false;
             break;
@@ -600,11 +630,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t bbase = smem_u32(sm + L.stages + s * 256 * 128);
+            const uint32_t bbase = smem_u32(sm + L.stages + s * D_STAGE);
 #pragma unroll
             for (int kk = 0; kk < KB / 16; ++kk)
-              mma_bf16(tmem + buf * 256, desc_k128(hbase + k2 * A_STAGE + kk * 32),
-                       desc_k128(bbase + kk * 32), id2, (k2 | kk) != 0);
+              mma_bf16_ta(tmem + TM_ACC + buf * DNT, tmem + (uint32_t)(k2 * 32 + kk * 8),
+                          desc_k128(bbase + kk * 32), id2, (k2 | kk) != 0);
             mma_commit(&empty[s]);
           }
           mma_commit(&acc_full[buf]);
@@ -618,121 +648,133 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int t_ = threadIdx.x;
     const int q = warp & 3, half = warp >> 2;
     const int r = q * 32 + lane;
-    const int sw = a.sw;
-    float* stg = reinterpret_cast<float*>(sm + L.stg) + warp * 32 * (sw + 1);
-    const int rpi = 32 / sw;                    // rows per store instruction
-    const int sub_r = lane / sw, sub_c = lane % sw;
-    int iter = 0, J = 0;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    uint8_t* obox = sm + L.stg + warp * 2 * D_OUT;  // this warp's two output boxes
+    int ob = 0;                                     // box the next TMA store reads
+    int J = 0;
     bool ok = true;
     for (long long t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
       TileInfo ti;
       if (!tile_info((int)t, a.n, a.G, a.goff, a.toff, ti)) continue;
       const int rows = (int)min((long long)BM, ti.mend - ti.m0);
-      const uint32_t tp = iter & 1;
-      // ---- D1 operands: latent tile [128][64] and W3 [H][64] (K zero-padded) ----
-      {
-        const __nv_bfloat16* W3 = a.W3 + ti.g * a.w3_gs;
-        // latent: 128 rows x 8 chunks of 16 B; chunk c holds k = 8c..8c+7
-        for (int idx = t_; idx < BM * 8; idx += NCONV * 32) {
+      // ---- first layer, chunk by chunk: operands, then h = act(acc + b3)
+      // as packed BF16 into tensor memory ----
+      // latent: 128 rows x 8 chunks of 16 B; chunk c holds k = 8c..8c+7
+      for (int idx = t_; idx < BM * 8; idx += NCONV * 32) {
+        const int rw = idx >> 3, c = idx & 7;
+        uint4 w = make_uint4(0, 0, 0, 0);
+        if (rw < rows && c * 8 < a.L)
+          w = *reinterpret_cast<const uint4*>(a.latent + (ti.m0 + rw) * a.L + c * 8);
+        *reinterpret_cast<uint4*>(sm + L.d1a + swz128(rw, c)) = w;
+      }
+      const __nv_bfloat16* W3 = a.W3 + ti.g * a.w3_gs;
+      const float* b3 = a.b3 + ti.g * a.b3_gs;
+      for (int ch = 0; ch < nchunk; ++ch, ++J) {
+        const int cw = min(DNT, H - ch * DNT), buf = J & 1;
+        // W3 rows [ch * 128, ch * 128 + cw), K zero-padded to 64 (the previous
+        // chunk's MMA has completed: its accumulator was drained below)
+        for (int idx = t_; idx < cw * 8; idx += NCONV * 32) {
           const int rw = idx >> 3, c = idx & 7;
           uint4 w = make_uint4(0, 0, 0, 0);
-          if (rw < rows && c * 8 < a.L)
-            w = *reinterpret_cast<const uint4*>(a.latent + (ti.m0 + rw) * a.L + c * 8);
-          *reinterpret_cast<uint4*>(sm + L.d1a + swz128(rw, c)) = w;
-        }
-        for (int idx = t_; idx < H * 8; idx += NCONV * 32) {
-          const int rw = idx >> 3, c = idx & 7;
-          uint4 w = make_uint4(0, 0, 0, 0);
-          if (c * 8 < a.L) w = *reinterpret_cast<const uint4*>(W3 + (long long)rw * a.L + c * 8);
-          // rows beyond 256 go to the second 256-row block (row r of block r / 256)
-          *reinterpret_cast<uint4*>(sm + L.d1b + (rw >> 8) * 256 * 128 + swz128(rw & 255, c)) = w;
+          if (c * 8 < a.L)
+            w = *reinterpret_cast<const uint4*>(W3 + (long long)(ch * DNT + rw) * a.L + c * 8);
+          *reinterpret_cast<uint4*>(sm + L.d1b + swz128(rw, c)) = w;
         }
         fence_proxy_async_smem();
         tc_fence_before();
         mbar_arrive(d1_ops);
-      }
-      // ---- D1 epilogue: h = act(acc + b3) -> BF16 swizzled h tile ----
-      if (!mbar_wait(d1_done, tp)) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      {
-        const float* b3 = a.b3 + ti.g * a.b3_gs;
-        const int c_lo = half * (H / 2), c_hi = c_lo + H / 2;
-        for (int c = c_lo; c < c_hi; c += 32) {
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
-          uint8_t* hb = sm + L.h + (c / KB) * A_STAGE;
-          const int ch0 = (c % KB) / 8;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            uint4 w;
-            w.x = pack_bf16(act_f(a.act, v[8 * u + 0] + __ldg(b3 + c + 8 * u + 0)),
-                            act_f(a.act, v[8 * u + 1] + __ldg(b3 + c + 8 * u + 1)));
-            w.y = pack_bf16(act_f(a.act, v[8 * u + 2] + __ldg(b3 + c + 8 * u + 2)),
-                            act_f(a.act, v[8 * u + 3] + __ldg(b3 + c + 8 * u + 3)));
-            w.z = pack_bf16(act_f(a.act, v[8 * u + 4] + __ldg(b3 + c + 8 * u + 4)),
-                            act_f(a.act, v[8 * u + 5] + __ldg(b3 + c + 8 * u + 5)));
-            w.w = pack_bf16(act_f(a.act, v[8 * u + 6] + __ldg(b3 + c + 8 * u + 6)),
-                            act_f(a.act, v[8 * u + 7] + __ldg(b3 + c + 8 * u + 7)));
-            *reinterpret_cast<uint4*>(hb + swz128(r, ch0 + u)) = w;
-          }
+        if (!mbar_wait(&acc_full[buf], (J >> 1) & 1)) {
+          ok = false;
+          break;
         }
+        tc_fence_after();
+        const int cpw = cw / 2;  // columns of the chunk per warp half
+        for (int col = half * cpw; col < (half + 1) * cpw; col += 32) {
+          float v[32];
+          tmem_ld32(tmem + lane_base + TM_ACC + (uint32_t)(buf * DNT + col), v);
+          const int hc = ch * DNT + col;
+          uint32_t u[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            u[i] = pack_bf16(act_f(a.act, v[2 * i] + __ldg(b3 + hc + 2 * i)),
+                             act_f(a.act, v[2 * i + 1] + __ldg(b3 + hc + 2 * i + 1)));
+          tmem_st16(tmem + lane_base + (uint32_t)(hc / 2), u);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive(&acc_empty[buf]);
       }
-      fence_proxy_async_smem();
+      if (!ok) break;
       tc_fence_before();
       mbar_arrive(h_full);
-      // ---- D2 epilogue per 256-column tile: xhat = s (acc + b4) ----
-      // each thread holds one row; the values go through a per-warp staging
-      // block so that every store instruction writes whole rows segments
+      // ---- second layer per 128-column tile: xhat = s (acc + b4) ----
+      // each thread holds one row; a warp's 32 rows x 32 columns go to shared
+      // memory in the layout of the TMA store and leave as one box.  A tile
+      // that ends inside the batch (its group ends mid-tile) takes plain
+      // stores through a transposition block instead: a box would also cover
+      // the first rows of the next group
       const float* b4 = a.b4 + ti.g * a.b4_gs;
       const float rs = r < rows ? (float)a.scale[ti.m0 + r] : 0.f;
+      const bool by_tma = a.tma && (rows == BM || ti.mend == a.n);
+      const bool warp_rows = q * 32 < rows;
       for (int j = 0; j < ntiles; ++j, ++J) {
         const int buf = J & 1;
         if (ok && (*abort_flag || !mbar_wait(&acc_full[buf], (J >> 1) & 1))) ok = false;
         if (ok) {
           tc_fence_after();
 #pragma unroll 1
-          for (int cc = 0; cc < 128; cc += 32) {
-            const int col = half * 128 + cc;
+          for (int cc = 0; cc < DNT / 2; cc += 32) {
+            const int col = half * (DNT / 2) + cc, p0 = j * DNT + col;
+            if (p0 >= a.P) break;
             float v[32];
-            tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + col), v);
-            const int p0 = j * 256 + col;
+            tmem_ld32(tmem + lane_base + TM_ACC + (uint32_t)(buf * DNT + col), v);
+            // b4 of the 32 columns: the same address in every lane
 #pragma unroll
-            for (int h0 = 0; h0 < 32; h0 += 16) {
-              if (sw == 16 || h0 == 0) {
-                __syncwarp();
-                const int nc = sw == 16 ? 16 : 32;
+            for (int i = 0; i < 32; i += 4) {
+              const float4 b = __ldg(reinterpret_cast<const float4*>(b4 + p0 + i));
+              v[i] = rs * (v[i] + (p0 + i < a.P ? b.x : 0.f));
+              v[i + 1] = rs * (v[i + 1] + (p0 + i + 1 < a.P ? b.y : 0.f));
+              v[i + 2] = rs * (v[i + 2] + (p0 + i + 2 < a.P ? b.z : 0.f));
+              v[i + 3] = rs * (v[i + 3] + (p0 + i + 3 < a.P ? b.w : 0.f));
+            }
+            if (by_tma) {
+              uint8_t* box = obox + ob * D_OUT;
+              if (lane == 0) bulk_wait_read<1>();  // the store that last read this box
+              __syncwarp();
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                  const int pc = p0 + h0 + i;
-                  stg[lane * (sw + 1) + i] = rs * (v[h0 + i] + (pc < a.P ? __ldg(b4 + pc) : 0.f));
-                }
-                if (nc == 32) {
-#pragma unroll
-                  for (int i = 16; i < 32; ++i) {
-                    const int pc = p0 + i;
-                    stg[lane * (sw + 1) + i] = rs * (v[i] + (pc < a.P ? __ldg(b4 + pc) : 0.f));
-                  }
-                }
-                __syncwarp();
-                // rows q*32 + rr .. of this warp, columns p0 + h0 + sub_c
-                const int pcol = p0 + (sw == 16 ? h0 : 0) + sub_c;
-                for (int rr = sub_r; rr < 32; rr += rpi) {
-                  const int row = q * 32 + rr;
-                  if (row < rows && pcol < a.P)
-                    a.xhat[(ti.m0 + row) * a.ld + pcol] = stg[rr * (sw + 1) + sub_c];
-                }
+              for (int c = 0; c < 8; ++c)
+                *reinterpret_cast<float4*>(box + swz128(lane, c)) =
+                    make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+              fence_proxy_async_smem();
+              __syncwarp();
+              if (lane == 0 && warp_rows) {
+                tma_store_2d(&mapX, box, p0, (int)(ti.m0 + q * 32));
+                bulk_commit();
               }
+              ob ^= 1;
+            } else {
+              float* tb = reinterpret_cast<float*>(obox);
+              if (lane == 0) bulk_wait_read<0>();
+              __syncwarp();
+#pragma unroll
+              for (int i = 0; i < 32; ++i) tb[lane * 33 + i] = v[i];
+              __syncwarp();
+              const int pc = p0 + lane;
+              for (int rr = 0; rr < 32; ++rr) {
+                const int row = q * 32 + rr;
+                if (row < rows && pc < a.P) a.xhat[(ti.m0 + row) * a.ld + pc] = tb[rr * 33 + lane];
+              }
+              __syncwarp();
             }
           }
         }
         tc_fence_before();
         mbar_arrive(&acc_empty[buf]);
       }
-      ++iter;
     }
+    // the boxes stay in shared memory until their stores have completed
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
     if (!ok) fail();
   }
   tc_fence_before();
@@ -778,6 +820,23 @@ int make_map(CUtensorMap* map, const void* base, int cols, int rows, int G, long
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(AEQC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return AEQC_OK;
+}
+
+// 2-D FP32 tensor [rows][cols] with row pitch ld elements, written in boxes of
+// 32 columns x 32 rows from a 128-byte-swizzled shared-memory layout; false
+// where the tensor map cannot describe the output (unaligned base or pitch)
+bool make_out_map(CUtensorMap* map, float* base, int cols, long long rows, long long ld) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld & 3) != 0 || ld < cols ||
+      rows <= 0 || rows > 0x7FFFFFFFll - BM)
+    return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t es[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -845,7 +904,7 @@ int run_decode_tc(aeqc_model* m, const void* latent, const double* scale, long l
   const aeqc_model_desc& d = m->d;
   const __nv_bfloat16* bf = static_cast<const __nv_bfloat16*>(m->inf_bf16);
   CUtensorMap mW4;
-  int rc = make_map(&mW4, bf + m->bD2B, d.H, d.P, d.n_groups, m->n_bf16, 256);
+  int rc = make_map(&mW4, bf + m->bD2B, d.H, d.P, d.n_groups, m->n_bf16, DNT);
   if (rc) return rc;
   DecArgs a;
   memset(&a, 0, sizeof(a));
@@ -868,21 +927,27 @@ int run_decode_tc(aeqc_model* m, const void* latent, const double* scale, long l
   a.xhat = xhat;
   a.ld = ld;
   a.err = err;
-  // deepest pipeline with the full staging width that fits, else half width
-  int ns = m->tuning.dec_stages >= 2 && m->tuning.dec_stages <= 4 ? m->tuning.dec_stages : 4;
-  int sw = 32;
-  while (ns > 2 && DecSmem(d.H, ns, sw).total + 1024 > 227 * 1024) --ns;
-  if (DecSmem(d.H, ns, sw).total + 1024 > 227 * 1024) sw = 16;
+  // full tiles of xhat leave through TMA stores where a tensor map can
+  // describe the output
+  CUtensorMap mX;
+  memset(&mX, 0, sizeof(mX));
+  a.tma = make_out_map(&mX, xhat, d.P, n, ld) ? 1 : 0;
+  // the W4 ring as deep as the shared memory allows next to the output boxes
+  // (h is in tensor memory, so H does not enter); the tuned decoder depth,
+  // when set, caps it
+  const int cap = m->tuning.dec_stages >= 2 && m->tuning.dec_stages <= 16 ? m->tuning.dec_stages
+                                                                          : 16;
+  int ns = 2;
+  while (ns < cap && DecSmem(ns + 1).total + 1024 <= 227 * 1024) ++ns;
   a.ns = ns;
-  a.sw = sw;
-  const size_t smem = DecSmem(d.H, ns, sw).total + 1024;
+  const size_t smem = DecSmem(ns).total + 1024;
   if (smem > 227 * 1024) return set_error(AEQC_EUNSUPPORTED, "decoder tile does not fit (H=%d)", d.H);
   {
     const int rc = raise_smem_limit((const void*)dec_tc_kernel, 227 * 1024);
     if (rc) return rc;
   }
   a.ntiles = G > 1 ? (n + BM - 1) / BM + G : (n + BM - 1) / BM;
-  dec_tc_kernel<<<persistent_grid(a.ntiles), NTHREADS, smem, s>>>(mW4, a);
+  dec_tc_kernel<<<persistent_grid(a.ntiles), NTHREADS, smem, s>>>(mW4, mX, a);
   return check_launch("dec_tc_kernel");
 }
 

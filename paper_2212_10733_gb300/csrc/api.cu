@@ -374,8 +374,8 @@ extern "C" int aeqc_model_set_tuning(aeqc_model* m, const aeqc_tuning* t) {
   AEQC_CHECK_ARG(m && t, "aeqc_model_set_tuning: null argument");
   AEQC_CHECK_ARG(t->enc_stages == 0 || (t->enc_stages >= 2 && t->enc_stages <= 6),
                  "aeqc_model_set_tuning: enc_stages must be 0 or in [2, 6]");
-  AEQC_CHECK_ARG(t->dec_stages == 0 || (t->dec_stages >= 2 && t->dec_stages <= 4),
-                 "aeqc_model_set_tuning: dec_stages must be 0 or in [2, 4]");
+  AEQC_CHECK_ARG(t->dec_stages == 0 || (t->dec_stages >= 2 && t->dec_stages <= 16),
+                 "aeqc_model_set_tuning: dec_stages must be 0 or in [2, 16]");
   AEQC_CHECK_ARG(t->qc_ctas_per_sm >= 0 && t->qc_ctas_per_sm <= 4,
                  "aeqc_model_set_tuning: qc_ctas_per_sm must be in [0, 4]");
   m->tuning = *t;
@@ -458,7 +458,7 @@ extern "C" int aeqc_autotune(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* grid
     t.enc_stages = bv;
     bt = 1e30f;
     bv = t.dec_stages;
-    for (int v = 2; v <= 4 && !rc; ++v) {
+    for (int v = 4; v <= 16 && !rc; v += 4) {
       m->tuning.dec_stages = v;
       float ms = 0.f;
       if ((rc = time_calls(s, reps, [&]() {

@@ -494,8 +494,10 @@ extern "C" int aeqc_model_create(const aeqc_model_desc* desc, aeqc_model** out) 
   m->bD2B = r; r += P * H;
   m->n_bf16 = (r + 63) / 64 * 64;
   const long long G = d.n_groups;
-  size_t bytes = sizeof(float) * (size_t)(G * m->n_group + 2 * G * m->n_train + G * m->n_inf) +
-                 256;  // + the device error word
+  // params, adam_m, adam_v contiguous (saved as one block); the inference
+  // copy starts on a 256-byte boundary (vector loads of its bias rows)
+  const long long inf_off = (G * m->n_group + 2 * G * m->n_train + 63) / 64 * 64;
+  size_t bytes = sizeof(float) * (size_t)(inf_off + G * m->n_inf) + 256;  // + the device error word
   size_t bbytes = d.dtype == AEQC_DTYPE_BF16 ? sizeof(__nv_bfloat16) * (size_t)(G * m->n_bf16) : 0;
   char* base = nullptr;
   if (cudaMalloc(&base, bytes) != cudaSuccess) {
@@ -510,7 +512,7 @@ extern "C" int aeqc_model_create(const aeqc_model_desc* desc, aeqc_model** out) 
   m->params = reinterpret_cast<float*>(base);
   m->adam_m = m->params + G * m->n_group;
   m->adam_v = m->adam_m + G * m->n_train;
-  m->inf = m->adam_v + G * m->n_train;
+  m->inf = m->params + inf_off;
   m->dev_err = reinterpret_cast<int*>(m->inf + G * m->n_inf);
   if (bbytes) {
     if (cudaMalloc(&m->inf_bf16, bbytes) != cudaSuccess) {

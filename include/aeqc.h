@@ -153,12 +153,13 @@ int aeqc_model_destroy(aeqc_model* m);
  *   enc_stages, dec_stages  pipeline depth of the BF16 tensor-core encoder /
  *                           decoder (2..6 / 2..16; reduced to what fits in
  *                           shared memory)
- *   qc_ctas_per_sm          CTAs of the correction kernel per SM (1..4) in
- *                           compress_batch and compress_batch_host */
+ *   qc_warps_per_sm         warps of the correction kernel per SM (4, 8, 12
+ *                           or 16; one CTA per SM) in compress_batch and
+ *                           compress_batch_host */
 typedef struct aeqc_tuning {
   int32_t enc_stages;
   int32_t dec_stages;
-  int32_t qc_ctas_per_sm;
+  int32_t qc_warps_per_sm;
   int32_t reserved;
 } aeqc_tuning;
 int aeqc_model_set_tuning(aeqc_model* m, const aeqc_tuning* t);

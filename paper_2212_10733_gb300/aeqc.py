@@ -70,7 +70,7 @@ class aeqc_model_desc(C.Structure):
 
 
 class aeqc_tuning(C.Structure):
-    _fields_ = [(n, C.c_int32) for n in ("enc_stages", "dec_stages", "qc_ctas_per_sm",
+    _fields_ = [(n, C.c_int32) for n in ("enc_stages", "dec_stages", "qc_warps_per_sm",
                                           "reserved")]
 
 
@@ -410,15 +410,15 @@ class Model:
                                    _ptr(ws), ws.numel(), _stream(stream)))
         return loss, g
 
-    def set_tuning(self, enc_stages: int = 0, dec_stages: int = 0, qc_ctas_per_sm: int = 0):
-        t = aeqc_tuning(enc_stages, dec_stages, qc_ctas_per_sm, 0)
+    def set_tuning(self, enc_stages: int = 0, dec_stages: int = 0, qc_warps_per_sm: int = 0):
+        t = aeqc_tuning(enc_stages, dec_stages, qc_warps_per_sm, 0)
         _check(load().aeqc_model_set_tuning(self.h, C.byref(t)))
 
     def get_tuning(self) -> dict:
         t = aeqc_tuning()
         _check(load().aeqc_model_get_tuning(self.h, C.byref(t)))
         return dict(enc_stages=t.enc_stages, dec_stages=t.dec_stages,
-                    qc_ctas_per_sm=t.qc_ctas_per_sm)
+                    qc_warps_per_sm=t.qc_warps_per_sm)
 
     def latent_dtype(self):
         import torch
@@ -618,7 +618,7 @@ def autotune(m: Model, grid: Grid, x, params: aeqc_params, mlp: Optional[MLP] = 
                                 C.byref(out.c), _ptr(ws), ws.numel(), _stream(stream),
                                 C.byref(t)))
     return dict(enc_stages=t.enc_stages, dec_stages=t.dec_stages,
-                qc_ctas_per_sm=t.qc_ctas_per_sm)
+                qc_warps_per_sm=t.qc_warps_per_sm)
 
 
 def compress_batch_workspace(m: Model, n: int, device):

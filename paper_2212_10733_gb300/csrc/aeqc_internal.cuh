@@ -160,7 +160,7 @@ int launch_fused_fp64_list(const FusedArgs& a, const int* list, const int* count
                            cudaStream_t s);
 // fast kernel + FP64 kernel over its deferred list; fb_list [n] and fb_count
 // are scratch in device memory
-int launch_fused_fast(const FusedArgs& a, cudaStream_t s, int ctas_per_sm = 0);
+int launch_fused_fast(const FusedArgs& a, cudaStream_t s, int warps_per_sm = 0);
 
 int launch_moments(const GridK& g, const double* x, long long n, double* Q, cudaStream_t s);
 int launch_quantize(const double* x, const float* xhat, long long ld, long long n, int P,

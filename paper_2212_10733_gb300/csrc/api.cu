@@ -120,7 +120,7 @@ static int run_quantize_correct(const GridK& gk, const ParamsK& pk, int kernel,
                                 aeqc_mlp* mlp, int latent_dtype, int latent_dim,
                                 aeqc_compressed* out, double* f_out, char* ws, size_t ws_bytes,
                                 cudaStream_t s, long long row0 = 0, bool reset_count = true,
-                                int ctas_per_sm = 0) {
+                                int warps_per_sm = 0) {
   WsCarver c(ws, ws_bytes);
   int* fb_list = c.take<int>((size_t)n);
   int* fb_count = c.take<int>(1);
@@ -152,7 +152,7 @@ static int run_quantize_correct(const GridK& gk, const ParamsK& pk, int kernel,
   if (rc) return rc;
   a.fb_list = fb_list;
   a.fb_count = fb_count;
-  return kernel == AEQC_KERNEL_FAST ? launch_fused_fast(a, s, ctas_per_sm)
+  return kernel == AEQC_KERNEL_FAST ? launch_fused_fast(a, s, warps_per_sm)
                                     : launch_fused_fp64(a, s);
 }
 
@@ -364,7 +364,7 @@ extern "C" int compress_batch(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* gri
     return rc;
   return run_quantize_correct(gk, pk, params->kernel, x, xhat, AEQC_XHAT_LD, n, mlp,
                               m->d.dtype, m->d.L, out, nullptr, rest, rest_bytes, s, 0, true,
-                              m->tuning.qc_ctas_per_sm);
+                              m->tuning.qc_warps_per_sm);
 }
 
 // ---- launch tuning --------------------------------------------------------------
@@ -376,8 +376,8 @@ extern "C" int aeqc_model_set_tuning(aeqc_model* m, const aeqc_tuning* t) {
                  "aeqc_model_set_tuning: enc_stages must be 0 or in [2, 6]");
   AEQC_CHECK_ARG(t->dec_stages == 0 || (t->dec_stages >= 2 && t->dec_stages <= 16),
                  "aeqc_model_set_tuning: dec_stages must be 0 or in [2, 16]");
-  AEQC_CHECK_ARG(t->qc_ctas_per_sm >= 0 && t->qc_ctas_per_sm <= 4,
-                 "aeqc_model_set_tuning: qc_ctas_per_sm must be in [0, 4]");
+  AEQC_CHECK_ARG(t->qc_warps_per_sm >= 0 && t->qc_warps_per_sm <= 16 && t->qc_warps_per_sm % 4 == 0,
+                 "aeqc_model_set_tuning: qc_warps_per_sm must be 0, 4, 8, 12 or 16");
   m->tuning = *t;
   m->tuning.reserved = 0;
   return AEQC_OK;
@@ -473,8 +473,8 @@ extern "C" int aeqc_autotune(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* grid
   }
   if (!rc && params->kernel == AEQC_KERNEL_FAST) {
     float bt = 1e30f;
-    int bv = t.qc_ctas_per_sm;
-    for (int v = 1; v <= 4; ++v) {
+    int bv = t.qc_warps_per_sm;
+    for (int v = 4; v <= 16; v += 4) {
       float ms = 0.f;
       if ((rc = time_calls(s, reps, [&]() {
              return run_quantize_correct(gk, pk, params->kernel, x, xhat, AEQC_XHAT_LD, n, mlp,
@@ -484,7 +484,7 @@ extern "C" int aeqc_autotune(aeqc_model* m, aeqc_mlp* mlp, const aeqc_grid* grid
         break;
       if (ms < bt) bt = ms, bv = v;
     }
-    t.qc_ctas_per_sm = bv;
+    t.qc_warps_per_sm = bv;
   }
   m->tuning = t;
   if (rc) return rc;
@@ -670,7 +670,7 @@ static int host_pipeline(aeqc_model* m, aeqc_mlp* mlp, const GridK& gk, const Pa
       break;
     if ((rc = run_quantize_correct(gk, pk, params->kernel, B.x, xhat, AEQC_XHAT_LD, rows, mlp,
                                    m->d.dtype, L, &dc, nullptr, rest, rest_bytes, s, c0,
-                                   false, m->tuning.qc_ctas_per_sm)))
+                                   false, m->tuning.qc_warps_per_sm)))
       break;
     AEQC_CUDA_TRY(cudaEventRecord(ev[b][1], s));
     // outputs

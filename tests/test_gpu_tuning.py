@@ -56,22 +56,22 @@ def same(a, b):
 
 def test_tuning_roundtrip_and_validation(aq, setup):
     m = setup[0]
-    m.set_tuning(enc_stages=3, dec_stages=2, qc_ctas_per_sm=2)
-    assert m.get_tuning() == dict(enc_stages=3, dec_stages=2, qc_ctas_per_sm=2)
+    m.set_tuning(enc_stages=3, dec_stages=2, qc_warps_per_sm=8)
+    assert m.get_tuning() == dict(enc_stages=3, dec_stages=2, qc_warps_per_sm=8)
     for bad in (dict(enc_stages=1), dict(enc_stages=7), dict(dec_stages=17),
-                dict(qc_ctas_per_sm=5)):
+                dict(qc_warps_per_sm=5), dict(qc_warps_per_sm=20)):
         with pytest.raises(RuntimeError):
             m.set_tuning(**bad)
     m.set_tuning()
-    assert m.get_tuning() == dict(enc_stages=0, dec_stages=0, qc_ctas_per_sm=0)
+    assert m.get_tuning() == dict(enc_stages=0, dec_stages=0, qc_warps_per_sm=0)
 
 
 def test_results_do_not_depend_on_tuning(aq, setup):
     m, grid, p, x, goff = setup
     ref = None
-    for t in (dict(), dict(enc_stages=2, dec_stages=2, qc_ctas_per_sm=1),
-              dict(enc_stages=5, dec_stages=3, qc_ctas_per_sm=3),
-              dict(enc_stages=4, dec_stages=16, qc_ctas_per_sm=2)):
+    for t in (dict(), dict(enc_stages=2, dec_stages=2, qc_warps_per_sm=4),
+              dict(enc_stages=5, dec_stages=3, qc_warps_per_sm=12),
+              dict(enc_stages=4, dec_stages=16, qc_warps_per_sm=8)):
         m.set_tuning(**t)
         out = aq.compress_batch(m, grid, x, p, group_offsets=goff, outlier_capacity=1 << 16)
         torch.cuda.synchronize()
@@ -91,7 +91,7 @@ def test_autotune_choice_is_valid_and_exact(aq, setup):
     best = aq.autotune(m, grid, x, p, group_offsets=goff, out=out)
     torch.cuda.synchronize()
     assert 2 <= best["enc_stages"] <= 6 and 2 <= best["dec_stages"] <= 16
-    assert 1 <= best["qc_ctas_per_sm"] <= 4
+    assert best["qc_warps_per_sm"] in (4, 8, 12, 16)
     assert m.get_tuning() == best
     same(ref, outputs(out))
     m.set_tuning()

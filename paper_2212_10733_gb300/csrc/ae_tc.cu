@@ -936,11 +936,12 @@ int run_decode_tc(aeqc_model* m, const void* latent, const double* scale, long l
   CUtensorMap mX;
   memset(&mX, 0, sizeof(mX));
   a.tma = make_out_map(&mX, xhat, d.P, n, ld) ? 1 : 0;
-  // the W4 ring as deep as the shared memory allows next to the output boxes
-  // (h is in tensor memory, so H does not enter); the tuned decoder depth,
-  // when set, caps it
+  // the W4 ring: the tuned depth, else four stages (measured at 1M histograms,
+  // H = 512: 2 / 4 / 6 / 8 stages 12.4 / 11.9 / 12.1 / 13.2 ms per 4M; deeper
+  // rings leave the SM less L1 cache for the bias, latent and W3 loads),
+  // reduced to what fits next to the output boxes
   const int cap = m->tuning.dec_stages >= 2 && m->tuning.dec_stages <= 16 ? m->tuning.dec_stages
-                                                                          : 16;
+                                                                          : 4;
   int ns = 2;
   while (ns < cap && DecSmem(ns + 1).total + 1024 <= 227 * 1024) ++ns;
   a.ns = ns;

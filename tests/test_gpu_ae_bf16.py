@@ -193,3 +193,49 @@ def test_bf16_persistent_tiles(aq, H, L, tied, sizes):
         _, xe, _ = emulate_decoder(prms[g], zg, sg, 0, tied)
         xsc = np.abs(xe).max(axis=1, keepdims=True) + 1e-30
         assert np.all(np.abs(xg - xe) <= 2e-3 * xsc), g
+
+
+def test_bf16_input_rounding_is_nearest_even(aq):
+    """The encoder's FP64 -> BF16 rounding of its input, seen through an
+    identity first layer and a second layer that selects 16 of its 64 hidden
+    units: with max(x) = 1 in every row (so 1/s = 1), latent l of row r is
+    exactly BF16(x[r, 4 l]).  The inputs hold BF16 ties, values one FP64 unit
+    either side of a tie, ties broken only by bits of the low 32-bit word,
+    zeros, negative and tiny (but float-normal) values, and random doubles."""
+    P = H = 64
+    L = 16
+    sel = np.arange(L) * 4
+    W2 = np.zeros((H, L))
+    W2[sel, np.arange(L)] = 1.0
+    p = dict(W1=np.eye(P), b1=np.zeros(H), W2=W2, b2=np.zeros(L), W3=np.zeros((L, H)),
+             b3=np.zeros(H), W4=np.zeros((H, P)), b4=np.zeros(P), mu=np.zeros(P),
+             sigma=np.ones(P))
+    m = aq.Model(P, H, L, tied=False, dtype=aq.DTYPE_BF16)
+    m.set_group(0, p)
+    rng = np.random.default_rng(11)
+    n = 4096
+    x = rng.uniform(0.0, 1.0, size=(n, P))
+    # BF16 values b in [2^-40, 1) and their half-unit ties
+    e = rng.integers(-40, 0, size=(n, L)).astype(np.float64)
+    b = np.ldexp(1.0 + rng.integers(0, 128, size=(n, L)) / 128.0, e.astype(int) - 1)
+    half = np.ldexp(1.0, e.astype(int) - 9)  # half a BF16 unit at b's binade
+    kind = rng.integers(0, 8, size=(n, L))
+    v = x[:, sel].copy()
+    v[kind == 0] = (b + half)[kind == 0]                                  # tie
+    v[kind == 1] = np.nextafter(b + half, np.inf)[kind == 1]              # just above
+    v[kind == 2] = np.nextafter(b + half, 0.0)[kind == 2]                 # just below
+    v[kind == 3] = (b + half * (1.0 + 2.0 ** -40))[kind == 3]             # low-word sticky bit
+    v[kind == 4] = 0.0
+    v[kind == 5] = -x[:, sel][kind == 5]
+    v[kind == 6] = np.ldexp(0.5 + 0.5 * x[:, sel], -100)[kind == 6]       # tiny, float-normal
+    x[:, sel] = v
+    x[:, P - 1] = 1.0
+    z, s = aq.ae_encode(m, dev(x))
+    torch.cuda.synchronize()
+    assert np.all(s.cpu().numpy() == 1.0)
+    got = z.float().cpu().numpy().astype(np.float64)
+    want = bf16_of_f64(x[:, sel])
+    bad = np.argwhere(got != want)
+    assert bad.size == 0, (bad[:5], x[:, sel][tuple(bad[0])], got[tuple(bad[0])],
+                           want[tuple(bad[0])])
+    m.close()

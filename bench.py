@@ -275,7 +275,39 @@ def build_workload(cfg, n, rank, device, aq, synth, train_steps=None):
     train_s = time.time() - t0
     tr = dict(train_steps=steps, batch=B, train_s=round(train_s, 3),
               histograms_per_s=round(steps * B / max(train_s, 1e-9), 1),
-              train_loss=float(loss.item()), optimizer="Adam lr 1e-3 (FP32 master weights)")
+              train_loss=float(loss.item()), optimizer="Adam lr 1e-3 (FP32 master weights)",
+              gemm="FP32 SIMT")
+    # the same training on the BF16 model: its GEMMs on the tensor cores
+    # (BF16 operands, FP32 accumulation), timed with CUDA events
+    steps_b = min(steps, 1024)
+    mb = aq.Model(P, H, L, tied=True, act=aq.ACT_IDENTITY, dtype=aq.DTYPE_BF16)
+    mb.set_group(0, synth.ae_init(P, H, L, seed))
+    mb.fit_normalizer(0, x[: min(n, 1 << 16)])
+    train_model(mb, x, 8, seed, B, device)
+    mb.set_group(0, synth.ae_init(P, H, L, seed))
+    mb.fit_normalizer(0, x[: min(n, 1 << 16)])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    loss_b, _ = train_model(mb, x, steps_b, seed, B, device)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    # 3 x (2 B H (P + L)) x 2 multiply-adds per weight: forward, dX and dW products
+    flop = 12.0 * B * H * (P + L) * steps_b
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    tf = flop / (ms_b / 1e3) / 1e12
+    tr["bf16_tensor_core"] = dict(
+        train_steps=steps_b, ms_per_step=round(ms_b / steps_b, 4),
+        histograms_per_s=round(steps_b * B / (ms_b / 1e3), 1),
+        train_loss=float(loss_b.item()),
+        gemm_tflops=round(tf, 2), tensor_frac=round(tf / peaks.get("bf16_tflops", 1900.0), 5),
+        device_status=mb.device_status(),
+        note="GEMMs: gemm_tc_kernel (tcgen05, 128x128 tiles); the batch of 128 gives "
+             "few tiles per product, so the step is latency-bound")
+    mb.close()
     if cfg.get("fit") == "closed_form":
         # the timed model: the exact minimiser of Eq. (5); the Adam run above
         # is reported against it on the same batch

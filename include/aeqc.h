@@ -119,7 +119,8 @@ const char* aeqc_version(void);
 
 /* ---- autoencoder model (Sec. III Stage 2, Sec. IV-B) ---------------------- */
 #define AEQC_DTYPE_F32 0  /* FP32 weights/activations, FP32 SIMT GEMMs */
-#define AEQC_DTYPE_BF16 1 /* BF16 weights/activations, FP32 accumulate, tcgen05 */
+#define AEQC_DTYPE_BF16 1 /* BF16 weights/activations, FP32 accumulate, tcgen05;
+                             training GEMMs with BF16 operands on tcgen05 too */
 
 #define AEQC_ACT_IDENTITY 0 /* the paper's linear activation */
 #define AEQC_ACT_RELU 1
@@ -165,6 +166,14 @@ typedef struct aeqc_tuning {
 int aeqc_model_set_tuning(aeqc_model* m, const aeqc_tuning* t);
 int aeqc_model_get_tuning(const aeqc_model* m, aeqc_tuning* t);
 
+/* Device status of the model's tensor-core kernels (encoder, decoder,
+ * training GEMMs): every wait inside them is bounded, and one that runs out
+ * sets the model's device status word instead of hanging.  Synchronises
+ * `stream`, copies the word to *status (0: no wait ran out since the last
+ * call; nonzero: the outputs of the calls since then are not valid) and
+ * clears it. */
+int aeqc_model_device_status(aeqc_model* m, int32_t* status, void* stream);
+
 /* Sets (synchronously) the parameters of one group from HOST float64 arrays:
  * W1 [P][H], b1 [H], W2 [H][L], b2 [L], b3 [H], b4 [P], mu [P], sigma [P]
  * (per-pixel Z-score of x / max(x), Sec. IV-C), and for untied models
@@ -192,8 +201,11 @@ size_t aeqc_fit_normalizer_workspace_size(const aeqc_model* m);
 
 /* One Adam step (lr, beta1 0.9, beta2 0.999, eps 1e-8) of group `group` on
  * the MSE of Eq. (5) between the normalised batch u = (x/max(x) - mu)/sigma
- * and its reconstruction, computed in FP32 by the library's own forward and
- * backward kernels.  x_batch [B][P] device float64.  loss_out (device float,
+ * and its reconstruction, computed by the library's own forward and backward
+ * kernels: FP32 SIMT GEMMs for an FP32 model; for a BF16 model the GEMMs run
+ * on the tensor cores with BF16-rounded operands and FP32 accumulation (the
+ * master weights, Adam and the elementwise steps stay FP32).  x_batch
+ * [B][P] device float64.  loss_out (device float,
  * may be NULL) receives the batch loss before the step. */
 int ae_train_step(aeqc_model* m, const double* x_batch, int64_t B, int32_t group,
                   float lr, float* loss_out, void* workspace, size_t workspace_bytes,

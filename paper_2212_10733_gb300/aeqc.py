@@ -94,6 +94,7 @@ SYMBOLS = {
     "aeqc_model_destroy": (C.c_int, [C.c_void_p]),
     "aeqc_model_set_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
     "aeqc_model_get_tuning": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "aeqc_model_device_status": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "aeqc_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                                 C.c_void_p, C.c_void_p]),
@@ -419,6 +420,14 @@ class Model:
         _check(load().aeqc_model_get_tuning(self.h, C.byref(t)))
         return dict(enc_stages=t.enc_stages, dec_stages=t.dec_stages,
                     qc_warps_per_sm=t.qc_warps_per_sm)
+
+    def device_status(self, stream=None) -> int:
+        """The model's device status word (nonzero: a bounded wait inside one
+        of its tensor-core kernels ran out since the last read); read and
+        cleared, synchronising the stream."""
+        v = C.c_int32(0)
+        _check(load().aeqc_model_device_status(self.h, C.byref(v), _stream(stream)))
+        return v.value
 
     def latent_dtype(self):
         import torch

@@ -390,6 +390,18 @@ extern "C" int aeqc_model_get_tuning(const aeqc_model* m, aeqc_tuning* t) {
   return AEQC_OK;
 }
 
+extern "C" int aeqc_model_device_status(aeqc_model* m, int32_t* status, void* stream) {
+  clear_error();
+  AEQC_CHECK_ARG(m && status, "aeqc_model_device_status: null argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  AEQC_CUDA_TRY(cudaMemcpyAsync(&v, m->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AEQC_CUDA_TRY(cudaMemsetAsync(m->dev_err, 0, sizeof(int), s));
+  AEQC_CUDA_TRY(cudaStreamSynchronize(s));
+  *status = v;
+  return AEQC_OK;
+}
+
 namespace aeqc {
 
 // mean time of `reps` calls of f after one untimed call, CUDA events on s

@@ -8,6 +8,7 @@
 
 #include <vector>
 
+#include "gemm_tc.cuh"
 #include "model.cuh"
 #include "workspace.cuh"
 
@@ -707,6 +708,22 @@ static int loss_grad_impl(aeqc_model* m, const double* x, int64_t B, int32_t gro
   float* par = m->params + group * m->n_group;
   const float *W1 = par + m->oW1, *b1 = par + m->ob1, *W2 = par + m->oW2, *b2 = par + m->ob2;
   const float *W3 = par + m->oW3, *b3 = par + m->ob3, *W4 = par + m->oW4, *b4 = par + m->ob4;
+  // the BF16 model trains on the tensor cores (BF16 operands, FP32
+  // accumulation; FP32 master weights and Adam), the FP32 model on FP32 SIMT
+  const bool tc = m->d.dtype == AEQC_DTYPE_BF16;
+  int* err = m->dev_err;
+  auto fwd = [&](long long M, int N, int K, const float* A, long long sam, const float* Bm,
+                 long long sbk, long long sbn, const float* bias, int ac, float* C,
+                 cudaStream_t st) {
+    return tc ? gemm_tc_bias(M, N, K, A, sam, Bm, sbk, sbn, bias, ac, C, err, st)
+              : gemm_bias(M, N, K, A, sam, Bm, sbk, sbn, bias, ac, C, st);
+  };
+  auto prod = [&](long long M, int N, int K, const float* A, long long sam, long long sak,
+                  const float* Bm, long long sbk, long long sbn, float* C, long long ldc,
+                  float beta, cudaStream_t st) {
+    return tc ? gemm_tc_plain(M, N, K, A, sam, sak, Bm, sbk, sbn, C, ldc, beta, err, st)
+              : gemm_plain(M, N, K, A, sam, sak, Bm, sbk, sbn, C, ldc, beta, st);
+  };
   int rc;
 #define TRY(e) \
   do {                    \
@@ -715,12 +732,12 @@ static int loss_grad_impl(aeqc_model* m, const double* x, int64_t B, int32_t gro
   normalize_kernel<<<(unsigned)B, 256, 0, s>>>(x, P, par + m->omu, par + m->osig, u);
   TRY(check_launch("normalize_kernel"));
   // forward: h1 = act(u W1 + b1); z = h1 W2 + b2; h3 = act(z W3' + b3); y = h3 W4' + b4
-  TRY(gemm_bias(B, H, P, u, P, W1, H, 1, b1, act, h1, s));
-  TRY(gemm_bias(B, L, H, h1, H, W2, L, 1, b2, AEQC_ACT_IDENTITY, z, s));
-  if (tied) TRY(gemm_bias(B, H, L, z, L, W2, 1, L, b3, act, h3, s));
-  else TRY(gemm_bias(B, H, L, z, L, W3, H, 1, b3, act, h3, s));
-  if (tied) TRY(gemm_bias(B, P, H, h3, H, W1, 1, H, b4, AEQC_ACT_IDENTITY, y, s));
-  else TRY(gemm_bias(B, P, H, h3, H, W4, P, 1, b4, AEQC_ACT_IDENTITY, y, s));
+  TRY(fwd(B, H, P, u, P, W1, H, 1, b1, act, h1, s));
+  TRY(fwd(B, L, H, h1, H, W2, L, 1, b2, AEQC_ACT_IDENTITY, z, s));
+  if (tied) TRY(fwd(B, H, L, z, L, W2, 1, L, b3, act, h3, s));
+  else TRY(fwd(B, H, L, z, L, W3, H, 1, b3, act, h3, s));
+  if (tied) TRY(fwd(B, P, H, h3, H, W1, 1, H, b4, AEQC_ACT_IDENTITY, y, s));
+  else TRY(fwd(B, P, H, h3, H, W4, P, 1, b4, AEQC_ACT_IDENTITY, y, s));
   // loss and dy
   mse_grad_kernel<<<(unsigned)B, 256, 0, s>>>(y, u, P, 2.f / ((float)B * (float)P), dy,
                                               rowloss);
@@ -733,10 +750,10 @@ static int loss_grad_impl(aeqc_model* m, const double* x, int64_t B, int32_t gro
   // layer 4
   colsum_kernel<<<(P + 255) / 256, 256, 0, s>>>(dy, B, P, gb4);
   TRY(check_launch("colsum_kernel"));
-  if (tied) TRY(gemm_plain(P, H, (int)B, dy, 1, P, h3, H, 1, gW1, H, 0.f, s));
-  else TRY(gemm_plain(H, P, (int)B, h3, 1, H, dy, P, 1, gW4, P, 0.f, s));
-  if (tied) TRY(gemm_plain(B, H, P, dy, P, 1, W1, H, 1, dh3, H, 0.f, s));
-  else TRY(gemm_plain(B, H, P, dy, P, 1, W4, 1, P, dh3, H, 0.f, s));
+  if (tied) TRY(prod(P, H, (int)B, dy, 1, P, h3, H, 1, gW1, H, 0.f, s));
+  else TRY(prod(H, P, (int)B, h3, 1, H, dy, P, 1, gW4, P, 0.f, s));
+  if (tied) TRY(prod(B, H, P, dy, P, 1, W1, H, 1, dh3, H, 0.f, s));
+  else TRY(prod(B, H, P, dy, P, 1, W4, 1, P, dh3, H, 0.f, s));
   if (act == AEQC_ACT_RELU) {
     relu_mask_kernel<<<256, 256, 0, s>>>(dh3, h3, (long long)B * H);
     TRY(check_launch("relu_mask_kernel"));
@@ -744,15 +761,15 @@ static int loss_grad_impl(aeqc_model* m, const double* x, int64_t B, int32_t gro
   // layer 3
   colsum_kernel<<<(H + 255) / 256, 256, 0, s>>>(dh3, B, H, gb3);
   TRY(check_launch("colsum_kernel"));
-  if (tied) TRY(gemm_plain(H, L, (int)B, dh3, 1, H, z, L, 1, gW2, L, 0.f, s));
-  else TRY(gemm_plain(L, H, (int)B, z, 1, L, dh3, H, 1, gW3, H, 0.f, s));
-  if (tied) TRY(gemm_plain(B, L, H, dh3, H, 1, W2, L, 1, dz, L, 0.f, s));
-  else TRY(gemm_plain(B, L, H, dh3, H, 1, W3, 1, H, dz, L, 0.f, s));
+  if (tied) TRY(prod(H, L, (int)B, dh3, 1, H, z, L, 1, gW2, L, 0.f, s));
+  else TRY(prod(L, H, (int)B, z, 1, L, dh3, H, 1, gW3, H, 0.f, s));
+  if (tied) TRY(prod(B, L, H, dh3, H, 1, W2, L, 1, dz, L, 0.f, s));
+  else TRY(prod(B, L, H, dh3, H, 1, W3, 1, H, dz, L, 0.f, s));
   // layer 2
   colsum_kernel<<<(L + 255) / 256, 256, 0, s>>>(dz, B, L, gb2);
   TRY(check_launch("colsum_kernel"));
-  TRY(gemm_plain(H, L, (int)B, h1, 1, H, dz, L, 1, gW2, L, tied ? 1.f : 0.f, s));
-  TRY(gemm_plain(B, H, L, dz, L, 1, W2, 1, L, dh1, H, 0.f, s));
+  TRY(prod(H, L, (int)B, h1, 1, H, dz, L, 1, gW2, L, tied ? 1.f : 0.f, s));
+  TRY(prod(B, H, L, dz, L, 1, W2, 1, L, dh1, H, 0.f, s));
   if (act == AEQC_ACT_RELU) {
     relu_mask_kernel<<<256, 256, 0, s>>>(dh1, h1, (long long)B * H);
     TRY(check_launch("relu_mask_kernel"));
@@ -760,7 +777,7 @@ static int loss_grad_impl(aeqc_model* m, const double* x, int64_t B, int32_t gro
   // layer 1
   colsum_kernel<<<(H + 255) / 256, 256, 0, s>>>(dh1, B, H, gb1);
   TRY(check_launch("colsum_kernel"));
-  TRY(gemm_plain(P, H, (int)B, u, 1, P, dh1, H, 1, gW1, H, tied ? 1.f : 0.f, s));
+  TRY(prod(P, H, (int)B, u, 1, P, dh1, H, 1, gW1, H, tied ? 1.f : 0.f, s));
   if (m->d.layers == 1) {  // the identity layer and its zero biases do not train
     AEQC_CUDA_TRY(cudaMemsetAsync(gW2, 0, sizeof(float) * (size_t)H * L, s));
     AEQC_CUDA_TRY(cudaMemsetAsync(gb2, 0, sizeof(float) * (size_t)L, s));

@@ -91,7 +91,8 @@ def parse():
     ap.add_argument("--train-steps", type=int, default=None,
                     help="override the number of autoencoder training steps")
     ap.add_argument("--profile", default=None,
-                    choices=["compress", "encode", "decode", "quantize_correct", "rice", "pq"],
+                    choices=["compress", "encode", "decode", "quantize_correct", "rice", "pq",
+                             "train_bf16"],
                     help="run --steps launches of one stage between cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off) and exit")
     return ap.parse_args()
@@ -433,11 +434,19 @@ def run_ours(args, rank, world, local):
             rs = aeqc.rice_encode(out.codes, ws=rws)
             aeqc.rice_decode(rs, synth.P)
 
+        mt = copy_model(aeqc, trained, cfg, aeqc.DTYPE_BF16)
+        xb = x[:cfg["batch"]].contiguous()
+        tws = [None]
+
+        def train_bf16():
+            tws[0] = mt.train_step(xb, lr=1e-3, ws=tws[0])
+
         fn = {"compress": lambda: aeqc.compress_batch(model, grid, x, prm, out=out, ws=ws),
               "encode": lambda: aeqc.ae_encode(model, x),
               "decode": lambda: aeqc.ae_decode(model, out.latent, out.scale),
               "quantize_correct": lambda: aeqc.quantize_correct(grid, x, xhat, prm, out=out),
               "rice": rice_round_trip,
+              "train_bf16": train_bf16,
               "pq": lambda: (aeqc.pq_train(out.latent, k=16, iters=10, table=tab),
                              aeqc.pq_encode(out.latent, tab, zq=zq))}
         for _ in range(args.warmup):

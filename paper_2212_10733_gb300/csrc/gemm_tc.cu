@@ -36,6 +36,8 @@ struct TcGemm {
   int bias_act, act;   // 1: C = act(acc + bias[n]); 0: C = alpha acc + beta C
   const float* bias;
   float alpha, beta;
+  int kbs;             // K blocks per split (blockIdx.z)
+  float* part;         // split K: raw FP32 tiles [split][M][N], else null
   int* err;
 };
 
@@ -44,16 +46,24 @@ struct TcGemm {
 __device__ __forceinline__ void fill_tile(uint8_t* dst, const float* src, long long sr,
                                           long long sk, int r0, int R, int k0, int K, int t) {
   const bool kfast = sk == 1;  // consecutive threads on consecutive k, else on consecutive r
-#pragma unroll 8
-  for (int i = 0; i < 128 * TKB / (TLOAD * 32); ++i) {
+  constexpr int PER = 128 * TKB / (TLOAD * 32);
+  // every load of the tile in flight before the first store
+  float v[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
     const int idx = t + i * (TLOAD * 32);
     const int r = kfast ? idx >> 6 : idx & 127;
     const int k = kfast ? idx & 63 : idx >> 7;
     const int gr = r0 + r, gk = k0 + k;
-    float v = 0.f;
-    if (gr < R && gk < K) v = __ldg(src + (long long)gr * sr + (long long)gk * sk);
+    v[i] = gr < R && gk < K ? __ldg(src + (long long)gr * sr + (long long)gk * sk) : 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int idx = t + i * (TLOAD * 32);
+    const int r = kfast ? idx >> 6 : idx & 127;
+    const int k = kfast ? idx & 63 : idx >> 7;
     *reinterpret_cast<__nv_bfloat16*>(dst + swz128(r, k >> 3) + (k & 7) * 2) =
-        __float2bfloat16_rn(v);
+        __float2bfloat16_rn(v[i]);
   }
 }
 
@@ -67,7 +77,10 @@ __global__ void __launch_bounds__(TTHREADS, 1) gemm_tc_kernel(const TcGemm a) {
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * TBM, n0 = blockIdx.y * TBN;
-  const int nk = (a.K + TKB - 1) / TKB;
+  // this CTA's K blocks (split K: a range of them, never empty)
+  const int kb_lo = blockIdx.z * a.kbs;
+  const int kb_hi = min((a.K + TKB - 1) / TKB, kb_lo + a.kbs);
+  const int nk = kb_hi - kb_lo;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TNS; ++s) {
@@ -115,8 +128,8 @@ __global__ void __launch_bounds__(TTHREADS, 1) gemm_tc_kernel(const TcGemm a) {
         break;
       }
       uint8_t* at = sm + s * 2 * T_TILE;
-      fill_tile(at, a.A, a.sam, a.sak, m0, a.M, kb * TKB, a.K, t);
-      fill_tile(at + T_TILE, a.B, a.sbn, a.sbk, n0, a.N, kb * TKB, a.K, t);
+      fill_tile(at, a.A, a.sam, a.sak, m0, a.M, (kb_lo + kb) * TKB, a.K, t);
+      fill_tile(at + T_TILE, a.B, a.sbn, a.sbk, n0, a.N, (kb_lo + kb) * TKB, a.K, t);
       fence_proxy_async_smem();
       tc_fence_before();
       mbar_arrive(&full[s]);
@@ -141,8 +154,12 @@ __global__ void __launch_bounds__(TTHREADS, 1) gemm_tc_kernel(const TcGemm a) {
         for (int rr = 0; rr < 32; ++rr) {
           const int m = m0 + q * 32 + rr;
           if (m < a.M && n < a.N) {
-            float* cp = a.C + (long long)m * a.ldc + n;
             float val = stg[rr * 33 + lane];
+            if (a.part) {  // split K: the raw sum of this K range
+              a.part[((long long)blockIdx.z * a.M + m) * a.N + n] = val;
+              continue;
+            }
+            float* cp = a.C + (long long)m * a.ldc + n;
             if (a.bias_act) {
               val += bn;
               if (a.act == AEQC_ACT_RELU) val = fmaxf(val, 0.f);
@@ -165,23 +182,68 @@ __global__ void __launch_bounds__(TTHREADS, 1) gemm_tc_kernel(const TcGemm a) {
   }
 }
 
-int launch_tc(const TcGemm& a, cudaStream_t s) {
+// split K: C = epi(sum over the splits of the partial tiles), summed in split
+// order (deterministic)
+__global__ void splitk_reduce_kernel(const TcGemm a, int splits) {
+  const long long mn = (long long)a.M * a.N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < mn;
+       i += (long long)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int z = 0; z < splits; ++z) acc += a.part[z * mn + i];
+    const int m = (int)(i / a.N), n = (int)(i - (long long)m * a.N);
+    float* cp = a.C + (long long)m * a.ldc + n;
+    if (a.bias_act) {
+      acc += a.bias ? __ldg(a.bias + n) : 0.f;
+      if (a.act == AEQC_ACT_RELU) acc = fmaxf(acc, 0.f);
+    } else {
+      acc = a.beta != 0.f ? fmaf(a.alpha, acc, a.beta * *cp) : a.alpha * acc;
+    }
+    *cp = acc;
+  }
+}
+
+int launch_tc(TcGemm a, float* scratch, long long scratch_elems, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0) return AEQC_OK;
   const int smem = TNS * 2 * T_TILE + 8 * (2 * TNS + 1) + 16 + 1024;
   {
     const int rc = raise_smem_limit((const void*)gemm_tc_kernel, smem);
     if (rc) return rc;
   }
-  dim3 grid((unsigned)((a.M + TBM - 1) / TBM), (unsigned)((a.N + TBN - 1) / TBN));
+  const int gx = (a.M + TBM - 1) / TBM, gy = (a.N + TBN - 1) / TBN;
+  const int nk = (a.K + TKB - 1) / TKB;
+  // few output tiles and a long K (the products with 128 batch rows and
+  // K = P or H): split K over more CTAs, at least two K blocks each, as far as
+  // the scratch holds the partial tiles
+  int splits = 1;
+  if (nk >= 4 && gx * gy < 64) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    splits = min(nk / 2, (sms + gx * gy - 1) / (gx * gy));
+    const long long mn = (long long)a.M * a.N;
+    if (scratch == nullptr || mn <= 0) splits = 1;
+    else if ((long long)splits * mn > scratch_elems) splits = (int)(scratch_elems / mn);
+    if (splits < 2) splits = 1;
+  }
+  a.kbs = (nk + splits - 1) / splits;
+  splits = nk > 0 ? (nk + a.kbs - 1) / a.kbs : 1;  // no empty split
+  a.part = splits > 1 ? scratch : nullptr;
+  dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)splits);
   gemm_tc_kernel<<<grid, TTHREADS, smem, s>>>(a);
-  return check_launch("gemm_tc_kernel");
+  int rc = check_launch("gemm_tc_kernel");
+  if (rc || splits == 1) return rc;
+  const long long mn = (long long)a.M * a.N;
+  const long long nb = (mn + 255) / 256 < 4096 ? (mn + 255) / 256 : 4096;
+  splitk_reduce_kernel<<<(unsigned)nb, 256, 0, s>>>(a, splits);
+  return check_launch("splitk_reduce_kernel");
 }
 
 }  // namespace
 
 int gemm_tc_plain(long long M, int N, int K, const float* A, long long sam, long long sak,
                   const float* B, long long sbk, long long sbn, float* C, long long ldc,
-                  float beta, int* err, cudaStream_t s) {
+                  float beta, float* scratch, long long scratch_elems, int* err,
+                  cudaStream_t s) {
   TcGemm a;
   memset(&a, 0, sizeof(a));
   a.M = (int)M; a.N = N; a.K = K;
@@ -191,12 +253,12 @@ int gemm_tc_plain(long long M, int N, int K, const float* A, long long sam, long
   a.alpha = 1.f;
   a.beta = beta;
   a.err = err;
-  return launch_tc(a, s);
+  return launch_tc(a, scratch, scratch_elems, s);
 }
 
 int gemm_tc_bias(long long M, int N, int K, const float* A, long long sam, const float* B,
-                 long long sbk, long long sbn, const float* bias, int act, float* C, int* err,
-                 cudaStream_t s) {
+                 long long sbk, long long sbn, const float* bias, int act, float* C,
+                 float* scratch, long long scratch_elems, int* err, cudaStream_t s) {
   TcGemm a;
   memset(&a, 0, sizeof(a));
   a.M = (int)M; a.N = N; a.K = K;
@@ -208,7 +270,12 @@ int gemm_tc_bias(long long M, int N, int K, const float* A, long long sam, const
   a.bias = bias;
   a.alpha = 1.f;
   a.err = err;
-  return launch_tc(a, s);
+  return launch_tc(a, scratch, scratch_elems, s);
+}
+
+long long gemm_tc_scratch_elems(long long B, int P, int H) {
+  const long long w = 16 * B * (long long)(P > H ? P : H);
+  return w < (1ll << 24) ? w : (1ll << 24);
 }
 
 }  // namespace aeqc

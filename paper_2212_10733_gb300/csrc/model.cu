@@ -673,6 +673,8 @@ extern "C" size_t ae_train_workspace_size(const aeqc_model* m, int64_t B) {
   w.add<float>(B);      // row losses
   w.add<float>(m->n_train);  // gradients
   w.add<float>(1);      // scratch loss
+  if (m->d.dtype == AEQC_DTYPE_BF16)  // split-K partial tiles of the tensor-core GEMMs
+    w.add<float>((size_t)gemm_tc_scratch_elems(B, (int)P, (int)H));
   return w.bytes;
 }
 
@@ -703,6 +705,9 @@ static int loss_grad_impl(aeqc_model* m, const double* x, int64_t B, int32_t gro
   float* rowloss = c.take<float>(B);
   float* grad = c.take<float>(m->n_train);
   float* lscratch = c.take<float>(1);
+  const long long kscr_n =
+      m->d.dtype == AEQC_DTYPE_BF16 ? gemm_tc_scratch_elems(B, m->d.P, m->d.H) : 0;
+  float* kscr = kscr_n ? c.take<float>((size_t)kscr_n) : nullptr;
   if (grad_ext) grad = grad_ext;
   *grad_used = grad;
   float* par = m->params + group * m->n_group;
@@ -715,13 +720,14 @@ static int loss_grad_impl(aeqc_model* m, const double* x, int64_t B, int32_t gro
   auto fwd = [&](long long M, int N, int K, const float* A, long long sam, const float* Bm,
                  long long sbk, long long sbn, const float* bias, int ac, float* C,
                  cudaStream_t st) {
-    return tc ? gemm_tc_bias(M, N, K, A, sam, Bm, sbk, sbn, bias, ac, C, err, st)
+    return tc ? gemm_tc_bias(M, N, K, A, sam, Bm, sbk, sbn, bias, ac, C, kscr, kscr_n, err, st)
               : gemm_bias(M, N, K, A, sam, Bm, sbk, sbn, bias, ac, C, st);
   };
   auto prod = [&](long long M, int N, int K, const float* A, long long sam, long long sak,
                   const float* Bm, long long sbk, long long sbn, float* C, long long ldc,
                   float beta, cudaStream_t st) {
-    return tc ? gemm_tc_plain(M, N, K, A, sam, sak, Bm, sbk, sbn, C, ldc, beta, err, st)
+    return tc ? gemm_tc_plain(M, N, K, A, sam, sak, Bm, sbk, sbn, C, ldc, beta, kscr, kscr_n,
+                              err, st)
               : gemm_plain(M, N, K, A, sam, sak, Bm, sbk, sbn, C, ldc, beta, st);
   };
   int rc;

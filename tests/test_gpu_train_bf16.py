@@ -101,3 +101,84 @@ def test_bf16_training_reduces_loss_like_fp32(aq):
     f32, b16 = losses[aq.DTYPE_F32], losses[aq.DTYPE_BF16]
     assert b16[1] < 0.5 * b16[0]
     assert abs(b16[1] - f32[1]) <= 0.05 * f32[1]
+
+
+def bf16(a):
+    """float32 -> nearest BF16 (ties to even), as float64."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def emulate_loss_grad(p, x, tied):
+    """The BF16 training step's arithmetic (identity activation) in numpy:
+    each product of BF16-rounded FP32 operands summed in FP64, rounded to
+    FP32 with its epilogue, the elementwise steps in FP32."""
+    f32 = np.float32
+    P = x.shape[1]
+    B = x.shape[0]
+    W1, b1, W2, b2 = (f32(p[k]) for k in ("W1", "b1", "W2", "b2"))
+    b3, b4 = f32(p["b3"]), f32(p["b4"])
+    W3 = W2.T if tied else f32(p["W3"])
+    W4 = W1.T if tied else f32(p["W4"])
+    mu, sig = f32(p["mu"]), f32(p["sigma"])
+    s = x.max(axis=1, keepdims=True)
+    u = f32((x * (1.0 / s) - mu.astype(np.float64)) / sig.astype(np.float64))
+    mm = lambda a, b: f32(bf16(a) @ bf16(b))
+    h1 = f32(mm(u, W1) + b1)
+    z = f32(mm(h1, W2) + b2)
+    h3 = f32(mm(z, W3) + b3)
+    y = f32(mm(h3, W4) + b4)
+    d = f32(y - u)
+    loss = float((d.astype(np.float64) ** 2).sum() / (B * P))
+    dy = f32(f32(2.0 / (B * P)) * d)
+    g = {"b4": dy.sum(axis=0, dtype=np.float64)}
+    if tied:
+        gW1 = mm(dy.T, h3)
+        dh3 = mm(dy, W1)
+    else:
+        g["W4"] = mm(h3.T, dy)
+        dh3 = mm(dy, W4.T)
+    g["b3"] = dh3.sum(axis=0, dtype=np.float64)
+    if tied:
+        gW2 = mm(dh3.T, z)
+        dz = mm(dh3, W2)
+    else:
+        g["W3"] = mm(z.T, dh3)
+        dz = mm(dh3, W3.T)
+    g["b2"] = dz.sum(axis=0, dtype=np.float64)
+    g["W2"] = f32(mm(h1.T, dz) + gW2) if tied else mm(h1.T, dz)
+    dh1 = mm(dz, W2.T)
+    g["b1"] = dh1.sum(axis=0, dtype=np.float64)
+    g["W1"] = f32(mm(u.T, dh1) + gW1) if tied else mm(u.T, dh1)
+    return loss, g
+
+
+@pytest.mark.parametrize("H,L,B,tied", [(128, 16, 200, True), (256, 32, 128, False)])
+def test_bf16_loss_grad_matches_bf16_emulation(aq, H, L, B, tied):
+    """Tight bar against the same BF16 arithmetic (the products that split
+    their K range over several CTAs included): loss within 1e-4 relative,
+    gradients within 2e-3 of each array's largest entry (FP32 summation order
+    and the rare BF16 rounding it flips)."""
+    P = 1521
+    prm = rand_params(P, H, L, tied, 23)
+    m = aq.Model(P, H, L, tied=tied, act=0, dtype=aq.DTYPE_BF16)
+    m.set_group(0, prm)
+    x = synth.histograms(B, synth.config_seed(5))
+    loss, g = m.loss_grad(dev(x))
+    torch.cuda.synchronize()
+    assert m.device_status() == 0
+    le, ge = emulate_loss_grad(prm, x, tied)
+    assert abs(loss.item() - le) <= 1e-4 * le
+    g = g.cpu().numpy().astype(np.float64)
+    order = ["W1", "b1", "W2", "b2"] + ([] if tied else ["W3"]) + ["b3"] + \
+            ([] if tied else ["W4"]) + ["b4"]
+    o = 0
+    for k in order:
+        ref = np.asarray(ge[k], dtype=np.float64).ravel()
+        got = g[o:o + ref.size]
+        o += ref.size
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err <= 2e-3, (k, err)
+    assert o == g.size
+    m.close()

@@ -533,10 +533,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int H = a.H, nk2 = H / KB, nchunk = (H + DNT - 1) / DNT;
   const int ntiles = (a.P + DNT - 1) / DNT;
-  // every CTA walks the output tiles from its own starting tile, so that the
-  // CTAs stream different parts of W4 at any moment instead of all
-  // requesting the same lines from L2
-  const int jrot = (int)(blockIdx.x % (unsigned)ntiles);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
@@ -572,7 +568,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (long long t = blockIdx.x; t < a.ntiles && ok && !*abort_flag; t += gridDim.x) {
         TileInfo ti;
         if (!tile_info((int)t, a.n, a.G, a.goff, a.toff, ti)) continue;
-        for (int jj = 0, j = jrot; jj < ntiles && ok; ++jj, j = j + 1 == ntiles ? 0 : j + 1)
+        for (int j = 0; j < ntiles && ok; ++j)
           for (int k2 = 0; k2 < nk2; ++k2, ++it) {
             const int s = it % ns;
             const uint32_t ph = (it / ns) & 1;
@@ -619,7 +615,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           break;
         }
         tc_fence_after();
-        for (int jj = 0; jj < ntiles && ok; ++jj, ++J) {
+        for (int j = 0; j < ntiles && ok; ++j, ++J) {
           const int buf = J & 1;
           if (J >= 2 && !mbar_wait(&acc_empty[buf], ((J >> 1) - 1) & 1)) {
             ok = false;
@@ -721,7 +717,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const float rs = r < rows ? (float)a.scale[ti.m0 + r] : 0.f;
       const bool by_tma = a.tma && (rows == BM || ti.mend == a.n);
       const bool warp_rows = q * 32 < rows;
-      for (int jj = 0, j = jrot; jj < ntiles; ++jj, ++J, j = j + 1 == ntiles ? 0 : j + 1) {
+      for (int j = 0; j < ntiles; ++j, ++J) {
         const int buf = J & 1;
         if (ok && (*abort_flag || !mbar_wait(&acc_full[buf], (J >> 1) & 1))) ok = false;
         if (ok) {

@@ -37,6 +37,13 @@ constexpr int WARP_TMA = 8;   // TMA producer, TMEM owner
 constexpr int WARP_MMA = 9;   // MMA issuer
 constexpr int NTHREADS = 320;
 constexpr uint32_t A_STAGE = BM * 128;  // bytes of one A stage (128 rows x 128 B)
+// the encoder: sixteen converter warps (eight rows of each A stage apiece),
+// then its TMA and MMA warps
+constexpr int ENC_NCONV = 16;
+constexpr int ENC_RPW = BM / ENC_NCONV;
+constexpr int ENC_WARP_TMA = ENC_NCONV;
+constexpr int ENC_WARP_MMA = ENC_NCONV + 1;
+constexpr int ENC_NTHREADS = (ENC_NCONV + 2) * 32;
 
 // error word values (device)
 constexpr int ERR_TIMEOUT = 1;
@@ -151,7 +158,7 @@ struct EncSmem {
 // tile iteration i waits on parity i & 1.  The BF16 h tile of the second MMA
 // aliases the stage ring, so the next tile's operand writes (A by the
 // converters, W1 and W2 by the TMA warp) start after lat_full of this tile.
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(ENC_NTHREADS, 1)
     enc_tc_kernel(const __grid_constant__ CUtensorMap mapW1,
                   const __grid_constant__ CUtensorMap mapW2, const EncArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -176,18 +183,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
-      mbar_init(&full_a[s], NCONV * 32);
+      mbar_init(&full_a[s], ENC_NCONV * 32);
       mbar_init(&full_b[s], 1);
       mbar_init(&empty[s], 1);
     }
     mbar_init(w2_full, 1);
     mbar_init(acc_full, 1);
-    mbar_init(h1_full, NCONV * 32);
+    mbar_init(h1_full, ENC_NCONV * 32);
     mbar_init(lat_full, 1);
     *abort_flag = 0;
     fence_barrier_init();
   }
-  if (warp == WARP_TMA) tmem_alloc(tmem_slot, tcols);
+  if (warp == ENC_WARP_TMA) tmem_alloc(tmem_slot, tcols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -198,7 +205,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     atomicExch(a.err, ERR_TIMEOUT);
   };
 
-  if (warp == WARP_TMA) {
+  if (warp == ENC_WARP_TMA) {
     if (lane == 0) {
       prefetch_tmap(&mapW1);
       prefetch_tmap(&mapW2);
@@ -236,7 +243,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
     __syncwarp();
-  } else if (warp == WARP_MMA) {
+  } else if (warp == ENC_WARP_MMA) {
     if (lane == 0) {
       const uint32_t id1 = idesc_bf16(BM, hn);
       const uint32_t id2 = idesc_bf16(BM, a.L);
@@ -281,8 +288,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     __syncwarp();
   } else {
-    // ---- converters / epilogue: eight warps ----
-    const int q = warp & 3, half = warp >> 2;
+    // ---- converters / epilogue: sixteen warps, ENC_RPW rows each ----
+    const int q = warp & 3, part = warp >> 2;
     const int r = q * 32 + lane;
     int it = 0, iter = 0;
     bool ok = true;
@@ -295,9 +302,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // signed 64-bit integers: exact among non-negative values (which order
       // like their bits) and below any of them for negatives; a row without a
       // non-negative value is redone exactly after the main loop
-      long long mraw[16];
+      long long mraw[ENC_RPW];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) mraw[i] = (long long)0x8000000000000000ull;
+      for (int i = 0; i < ENC_RPW; ++i) mraw[i] = (long long)0x8000000000000000ull;
       for (int kb = 0; kb < nkb; ++kb, ++it) {
         const int s = it % ns;
         const uint32_t ph = (it / ns) & 1;
@@ -307,10 +314,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         uint8_t* ast = sm + s * L.stage_bytes;
         const int k0 = kb * KB + 2 * lane;
-        unsigned long long v0[16], v1[16];
+        unsigned long long v0[ENC_RPW], v1[ENC_RPW];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int rw = warp * 16 + i;
+        for (int i = 0; i < ENC_RPW; ++i) {
+          const int rw = warp * ENC_RPW + i;
           v0[i] = 0;
           v1[i] = 0;
           if (rw < rows) {
@@ -321,8 +328,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int rw = warp * 16 + i;
+        for (int i = 0; i < ENC_RPW; ++i) {
+          const int rw = warp * ENC_RPW + i;
           if (k0 < a.P) mraw[i] = max(mraw[i], (long long)v0[i]);
           if (k0 + 1 < a.P) mraw[i] = max(mraw[i], (long long)v1[i]);
           const uint32_t packed =
@@ -335,13 +342,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_arrive(&full_a[s]);
       }
       if (!ok) break;
-      // row maxima: lanes hold partial maxima of rows warp*16 + i
+      // row maxima: lanes hold partial maxima of rows warp * ENC_RPW + i
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < ENC_RPW; ++i) {
         long long k = mraw[i];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) k = max(k, (long long)__shfl_xor_sync(0xffffffffu, k, o));
-        const int rw = warp * 16 + i;
+        const int rw = warp * ENC_RPW + i;
         if (k < 0 && rw < rows) {
           // no non-negative value: the exact maximum on order-preserving keys
           const double* xr = a.x + (ti.m0 + rw) * (long long)a.P;
@@ -356,7 +363,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         if (lane == 0) rowmax[rw] = __longlong_as_double(k);
       }
-      named_sync(1, NCONV * 32);
+      named_sync(1, ENC_NCONV * 32);
       // ---- E1 epilogue: TMEM -> act(acc / s + b1) -> BF16 swizzled h tile ----
       if (!mbar_wait(acc_full, tp)) {
         ok = false;
@@ -367,8 +374,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const double srow = rowmax[r];
         const float rs = (srow > 0.0 && isfinite(srow)) ? (float)(1.0 / srow) : 0.f;
         const float* b1 = a.b1 + ti.g * a.b1_gs;
-        const int c_lo = half * (H / 2), c_hi = c_lo + H / 2;
-        for (int c = c_lo; c < c_hi; c += 32) {
+        // 32-column slices of h, dealt round robin to the four warps of a
+        // lane quarter
+        for (int c = part * 32; c < H; c += 4 * 32) {
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
           uint8_t* hb = sm + (c / KB) * A_STAGE;
@@ -410,7 +418,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               dst[l >> 1] = pack_bf16(v[l] + __ldg(b2 + l), v[l + 1] + __ldg(b2 + l + 1));
           }
         }
-      } else {
+      } else if (warp < 8) {
         const int rr = (warp - 4) * 32 + lane;
         if (rr < rows) a.scale[ti.m0 + rr] = rowmax[rr];
       }
@@ -421,7 +429,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == WARP_TMA) {
+  if (warp == ENC_WARP_TMA) {
     tc_fence_after();
     tmem_dealloc(tmem, tcols);
   }
@@ -894,7 +902,7 @@ int run_encode_tc(aeqc_model* m, const double* x, long long n, const long long* 
     if (rc) return rc;
   }
   a.ntiles = G > 1 ? (n + BM - 1) / BM + G : (n + BM - 1) / BM;
-  enc_tc_kernel<<<persistent_grid(a.ntiles), NTHREADS, smem, s>>>(mW1, mW2, a);
+  enc_tc_kernel<<<persistent_grid(a.ntiles), ENC_NTHREADS, smem, s>>>(mW1, mW2, a);
   return check_launch("enc_tc_kernel");
 }
 

@@ -11,6 +11,11 @@ namespace {
 
 constexpr int BM = 128, BN = 128, BK = 8, NT = 256;
 
+// the narrow-layer kernel below takes the row-scale layer with N <= 8
+#define A_NARROW_OK(a)                                                                    \
+  ((a).a_f64 && (a).epi == EPI_ROWSCALE_BIAS_ACT && (a).N <= 8 && (a).sak == 1 &&         \
+   (a).M < (1ll << 36))
+
 __device__ __forceinline__ float act_apply(int act, float v) {
   return act == AEQC_ACT_RELU ? fmaxf(v, 0.f) : v;
 }
@@ -210,8 +215,148 @@ __global__ void tile_offsets_kernel(const long long* group_off, int G, int tile_
 
 }  // namespace
 
+// The first encoder layer of a narrow network (N <= 8 outputs, FP64 input
+// rows with unit stride, the row-scale epilogue): the 128 x 128 tiles above
+// would leave most of their FMAs idle, so one warp takes one row instead:
+// lanes stride over k, accumulate N products each and the row maximum (on the
+// bit patterns: non-negative doubles up to +inf order like their bits, so the
+// maximum over them and +0 is the FP64 "d > max" maximum, NaN and negatives
+// never winning), then reduce across the warp.  Same epilogue as above.
+template <int NN>
+__global__ void __launch_bounds__(256) rowscale_narrow_kernel(const GemmArgs a) {
+  const int lane = threadIdx.x & 31;
+  const long long m = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (m >= a.M) return;
+  int g = 0;
+  if (a.n_groups > 1) {  // last group whose first row <= m
+    int lo = 0, hi = a.n_groups;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (a.group_off[mid] <= m) lo = mid;
+      else hi = mid;
+    }
+    g = lo;
+  }
+  const double* Ar = static_cast<const double*>(a.A) + m * a.sam;
+  const float* B = a.B + (long long)g * a.group_stride_B;
+  const float* bias = a.bias ? a.bias + (long long)g * a.group_stride_bias : nullptr;
+  float acc[NN];
+#pragma unroll
+  for (int n = 0; n < NN; ++n) acc[n] = 0.f;
+  unsigned long long kmax = 0ull;  // +0
+  for (int k = lane; k < a.K; k += 32) {
+    const double d = __ldg(Ar + k);
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    if (u <= 0x7FF0000000000000ull && u > kmax) kmax = u;
+    const float v = (float)d;
+#pragma unroll
+    for (int n = 0; n < NN; ++n)
+      if (n < a.N) acc[n] = fmaf(v, __ldg(B + (long long)k * a.sbk + (long long)n * a.sbn), acc[n]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ko = __shfl_xor_sync(0xffffffffu, kmax, o);
+    kmax = ko > kmax ? ko : kmax;
+#pragma unroll
+    for (int n = 0; n < NN; ++n) acc[n] += __shfl_xor_sync(0xffffffffu, acc[n], o);
+  }
+  const double sm = __longlong_as_double((long long)kmax);
+  const float rs = (sm > 0.0 && isfinite(sm)) ? (float)(1.0 / sm) : 0.f;
+  if (lane == 0 && a.scale_out) a.scale_out[m] = sm;
+#pragma unroll
+  for (int n = 0; n < NN; ++n)
+    if (lane == n && n < a.N)
+      a.C[m * a.ldc + n] = act_apply(a.act, fmaf(acc[n], rs, bias ? __ldg(bias + n) : 0.f));
+}
+
+// The last decoder layer of a narrow network (K <= 8 inputs, the denormalising
+// epilogue): one warp per row, the row's K inputs held by every lane, lanes
+// over the output columns (coalesced stores); each output sums its K
+// products in k order from zero, as the tiled kernel does.
+template <int KK>
+__global__ void __launch_bounds__(256) denorm_narrow_kernel(const GemmArgs a) {
+  const int lane = threadIdx.x & 31;
+  const long long m = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (m >= a.M) return;
+  int g = 0;
+  if (a.n_groups > 1) {
+    int lo = 0, hi = a.n_groups;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (a.group_off[mid] <= m) lo = mid;
+      else hi = mid;
+    }
+    g = lo;
+  }
+  const float* Ar = static_cast<const float*>(a.A) + m * a.sam;
+  const float* B = a.B + (long long)g * a.group_stride_B;
+  const float* bias = a.bias ? a.bias + (long long)g * a.group_stride_bias : nullptr;
+  float av[KK];
+#pragma unroll
+  for (int k = 0; k < KK; ++k) av[k] = k < a.K ? __ldg(Ar + k) : 0.f;
+  const float rs = (float)a.scale_in[m];
+  float* Cr = a.C + m * a.ldc;
+  for (int n = lane; n < a.N; n += 32) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < KK; ++k)
+      if (k < a.K) acc = fmaf(av[k], __ldg(B + (long long)k * a.sbk + (long long)n * a.sbn), acc);
+    Cr[n] = rs * (acc + (bias ? __ldg(bias + n) : 0.f));
+  }
+}
+
+// A layer of at most 8 inputs and 8 outputs (the narrow network's middle
+// layers): one thread per row, each output summing its K products in k order
+// from zero, as the tiled kernel does.
+__global__ void __launch_bounds__(256) bias_act_tiny_kernel(const GemmArgs a) {
+  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= a.M) return;
+  int g = 0;
+  if (a.n_groups > 1) {
+    int lo = 0, hi = a.n_groups;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (a.group_off[mid] <= m) lo = mid;
+      else hi = mid;
+    }
+    g = lo;
+  }
+  const float* Ar = static_cast<const float*>(a.A) + m * a.sam;
+  const float* B = a.B + (long long)g * a.group_stride_B;
+  const float* bias = a.bias ? a.bias + (long long)g * a.group_stride_bias : nullptr;
+  float av[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) av[k] = k < a.K ? Ar[k] : 0.f;
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    if (n >= a.N) break;
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < a.K) acc = fmaf(av[k], __ldg(B + (long long)k * a.sbk + (long long)n * a.sbn), acc);
+    a.C[m * a.ldc + n] = act_apply(a.act, acc + (bias ? __ldg(bias + n) : 0.f));
+  }
+}
+
 int launch_gemm(const GemmArgs& a, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0) return AEQC_OK;
+  if (!a.a_f64 && a.epi == EPI_BIAS_ACT && a.N <= 8 && a.K <= 8 && a.sak == 1 &&
+      a.M < (1ll << 40)) {
+    bias_act_tiny_kernel<<<(unsigned)((a.M + 255) / 256), 256, 0, s>>>(a);
+    return check_launch("bias_act_tiny_kernel");
+  }
+  if (!a.a_f64 && a.epi == EPI_DENORM && a.K <= 8 && a.sak == 1 && a.M < (1ll << 36)) {
+    const unsigned blocks = (unsigned)((a.M + 7) / 8);
+    if (a.K <= 4) denorm_narrow_kernel<4><<<blocks, 256, 0, s>>>(a);
+    else denorm_narrow_kernel<8><<<blocks, 256, 0, s>>>(a);
+    return check_launch("denorm_narrow_kernel");
+  }
+  if (A_NARROW_OK(a)) {
+    const unsigned blocks = (unsigned)((a.M + 7) / 8);
+    if (a.N <= 4) rowscale_narrow_kernel<4><<<blocks, 256, 0, s>>>(a);
+    else rowscale_narrow_kernel<8><<<blocks, 256, 0, s>>>(a);
+    return check_launch("rowscale_narrow_kernel");
+  }
   long long tiles = a.n_groups <= 1 ? (a.M + BM - 1) / BM : a.max_tiles;
   if (tiles > 2147483647LL || tiles > 65535LL * 65535LL)
     return set_error(AEQC_EUNSUPPORTED, "gemm: too many row tiles");

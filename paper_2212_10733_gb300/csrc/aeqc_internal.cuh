@@ -119,6 +119,7 @@ struct FastGridK {
   float vol_h, vol_l;
   float d2q_h[3], d2q_l[3];
   float coef_h[5][5], coef_l[5][5];
+  float b_f, c0_f;   // b and c0 as floats
   float vmax, wmax;  // max |v_par| and max v_perp^2 on the grid
   float wk[4];       // vol sum |phi_k| over the grid (bounds of per-point rounding)
   // lane segments of the column walk (no integer division on the device):

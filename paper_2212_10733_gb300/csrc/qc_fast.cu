@@ -433,7 +433,7 @@ __device__ void phase_a(const GridK& g, const FastGridK& fg, const double* xb,
     for (int r = 0; r < 3; ++r) U[r] = c1.u[0] * p1[r] + c2.u[0] * p2[r];
     U[3] = c1.u[1] + c2.u[1];
   }
-  const float b_f = (float)fg.b, c0_f = (float)fg.c0;
+  const float b_f = fg.b_f, c0_f = fg.c0_f;
   float s1 = c1.xs * fabsf(fmaf(b_f, small_int_to_float(sg1.c - fg.i_c), c0_f)) +
              c2.xs * fabsf(fmaf(b_f, small_int_to_float(sg2.c - fg.i_c), c0_f));
   __syncwarp();
@@ -509,6 +509,9 @@ struct PassOut {
   float Habs[4];  // bounds on the sums of |terms| (for the FP32 rounding bound)
   float tmax;     // bound on |t| over the grid points (segment end points)
   float errmax;   // largest FP32 check value |x' e^{-t} - x| of the points
+  // row (lane & 3) of J = dH/dlambda = sum vol phi phi^T x' h'(t), in FP32
+  // (its rounding is bounded in the certificate of round1_fast)
+  float J[4];
   int viol, uncertain;
 };
 
@@ -545,16 +548,21 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
                           int lane, const bool EXACT) {
   df a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};  // sums of y, y ic, y ic^2, y j^2
   float ab1 = 0.f, tmax = 0.f, errmax = 0.f;
+  // sums of z = x' h'(t) over the monomials v^p w^q of phi phi^T, in the
+  // order m00 m10 m20 m30 m40 m01 m11 m21 m02 (w^q as j^(2q), d2^q later)
+  float jz[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const float cq = c.dl_f * 3.0517578125e-05f, dq = -12582912.f * cq;  // Delta 2^-15
-  // x' h(t) and the check value of one point (the largest check value decides
-  // the check after the walk)
-  auto point = [&](int p, float t) -> float {
+  // x' h(t), x' h'(t) and the check value of one point (the largest check
+  // value decides the check after the walk); h'(t) = 1 - e^-t = t - h(t)
+  auto point = [&](int p, float t, float& z) -> float {
     const float xp = w.xp[p];
     const float h =
         t * t * fmaf(-t, fmaf(-t, fmaf(-t, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f), 0.5f);
     // Delta rho from its 2^-15 fixed point: exact, see small_int_to_float
     const float drho = fmaf(__int_as_float(0x4B400000 + (int)w.rho[p]), cq, dq);
-    errmax = fmaxf(errmax, fabsf(fmaf(xp, h - t, -drho)));
+    const float hmt = h - t;
+    errmax = fmaxf(errmax, fabsf(fmaf(xp, hmt, -drho)));
+    z = -xp * hmt;
     return xp * h;
   };
   Seg sg[2];
@@ -570,6 +578,7 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
     A = df_add(A, df_mul_f(df{tc.h[3], tc.l[3]}, ic2f));
     const float ah = A.hi, al = A.lo;
     df s0 = {0.f, 0.f}, s3 = {0.f, 0.f};
+    float z0 = 0.f, z1 = 0.f, z2 = 0.f;  // sums of z, z j^2, z j^4
     float jf = small_int_to_float(sgm.j0), j2f = jf * jf;
     // |t| is largest at an end of the segment (t is monotone in j^2): a bound
     // over every point of the segment, x' = 0 included
@@ -580,7 +589,11 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
     int p = sgm.j0 * g.n_par + sgm.c;
     for (int j = sgm.j0; j < sgm.j1; ++j, p += g.n_par) {
       const float t = fmaf(tc.h[2], j2f, ah) + fmaf(tc.l[2], j2f, al);
-      const float y = point(p, t);
+      float z;
+      const float y = point(p, t, z);
+      z0 += z;
+      z1 = fmaf(z, j2f, z1);
+      z2 = fmaf(z, j2f * j2f, z2);
       if (EXACT) {
         s0 = df_add_f(s0, y);
         s3 = df_add_f(s3, y * j2f);
@@ -603,6 +616,39 @@ __device__ void pass_warp(const GridK& g, const FastGridK& fg, const FastWS& w,
       a[3].hi += s3.hi;
     }
     ab1 = fmaf(s0.hi, fabsf(icf), ab1);  // y >= 0
+    {
+      // the segment's column at v = b ic + c0 (FP32: J only enters the
+      // certificate with its rounding bounded)
+      const float v = fmaf(fg.b_f, icf, fg.c0_f), v2 = v * v;
+      jz[0] += z0;
+      jz[1] = fmaf(z0, v, jz[1]);
+      jz[2] = fmaf(z0, v2, jz[2]);
+      jz[3] = fmaf(z0, v2 * v, jz[3]);
+      jz[4] = fmaf(z0, v2 * v2, jz[4]);
+      jz[5] += z1;
+      jz[6] = fmaf(z1, v, jz[6]);
+      jz[7] = fmaf(z1, v2, jz[7]);
+      jz[8] += z2;
+    }
+  }
+  // warp totals of the J sums; lane k (mod 4) keeps row k of J:
+  // J[k][l] = vol d2^q m(p, q) for phi_k phi_l = v^p w^q
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) jz[i] += __shfl_xor_sync(FULL, jz[i], o);
+  }
+  {
+    const float vh = fg.vol_h, vd = vh * fg.d2q_h[1], vdd = vh * fg.d2q_h[2];
+    const float m00 = vh * jz[0], m10 = vh * jz[1], m20 = vh * jz[2], m30 = vh * jz[3],
+                m40 = vh * jz[4], m01 = vd * jz[5], m11 = vd * jz[6], m21 = vd * jz[7],
+                m02 = vdd * jz[8];
+    const int k = lane & 3;
+    // rows: (1, v, w, v^2) times (1, v, w, v^2)
+    o.J[0] = k == 0 ? m00 : (k == 1 ? m10 : (k == 2 ? m01 : m20));
+    o.J[1] = k == 0 ? m10 : (k == 1 ? m20 : (k == 2 ? m11 : m30));
+    o.J[2] = k == 0 ? m01 : (k == 1 ? m11 : (k == 2 ? m02 : m21));
+    o.J[3] = k == 0 ? m20 : (k == 1 ? m30 : (k == 2 ? m21 : m40));
   }
   // warp totals of the four sums, scattered (total k in lanes 8k..8k+7), in
   // double-float; then H_k in lane k and every total and H broadcast
@@ -771,6 +817,7 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
   float erel = 0.f;
   for (int it = 0;; ++it) {
     df H[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    float Jr[4] = {0.f, 0.f, 0.f, 0.f};  // row kr of dH/dlambda at lambda (after a pass)
     const bool zero_lam =
         lam[0].hi == 0.f && lam[1].hi == 0.f && lam[2].hi == 0.f && lam[3].hi == 0.f;
     int viol = 0, unc = 0;
@@ -806,6 +853,7 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         H[k] = po.H[k];
+        Jr[k] = po.J[k];
         eh = fmaxf(eh, hrel * po.Habs[k] * invS[k]);
       }
       erel += eh + 1.2e-13f * tb * po.tmax;
@@ -817,14 +865,18 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
       pmargin = margin;
     };
     if (!zero_lam || force_pass) do_pass();
-    // g_k = -R_k - (M lambda)_k + H_k, row k in lane k, gathered
+    // g_k = -R_k - (M lambda)_k + H_k, row k in lane k, gathered; at
+    // lambda = 0, g = -R (t = 0 on every point, so H = 0 even after a pass)
     df gk[4];
     {
-      df ml = df_mul(rowM[0], lam[0]);
+      df gl = df_neg(Rk);
+      if (!zero_lam) {
+        df ml = df_mul(rowM[0], lam[0]);
 #pragma unroll
-      for (int l = 1; l < 4; ++l) ml = df_add(ml, df_mul(rowM[l], lam[l]));
-      const df Hk = kr == 0 ? H[0] : (kr == 1 ? H[1] : (kr == 2 ? H[2] : H[3]));
-      const df gl = df_add(df_neg(df_add(Rk, ml)), Hk);
+        for (int l = 1; l < 4; ++l) ml = df_add(ml, df_mul(rowM[l], lam[l]));
+        const df Hk = kr == 0 ? H[0] : (kr == 1 ? H[1] : (kr == 2 ? H[2] : H[3]));
+        gl = df_add(df_neg(df_add(Rk, ml)), Hk);
+      }
 #pragma unroll
       for (int k = 0; k < 4; ++k)
         gk[k] = df{__shfl_sync(FULL, gl.hi, k), __shfl_sync(FULL, gl.lo, k)};
@@ -862,11 +914,19 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
       return 1;
     }
     if (it == max_iter) return 0;
-    // chord step with one refinement: delta = M^-1 g, then M^-1 (g - M delta)
-    float r[4], d1[4], d2[4];
+    // chord step with one refinement: delta = M^-1 g, then M^-1 (g - M delta).
+    // The first step from lambda = 0 goes without the refinement: its FP32
+    // error (~1e-6 of the step) is part of g at the next lambda, where the
+    // pass measures it and the next step removes it.
+    float r[4], d1[4], d2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int k = 0; k < 4; ++k) r[k] = gk[k].hi;
     chol_solve(ch, r, d1);
+    if (zero_lam) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) lam[k] = df{step * d1[k], 0.f};
+      continue;
+    }
     {
       df md = df_mul_f(rowM[0], d1[0]);
 #pragma unroll
@@ -877,33 +937,62 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
       for (int k = 0; k < 4; ++k) r[k] = __shfl_sync(FULL, rl, k);
     }
     chol_solve(ch, r, d2);
-    // Certificate after a pass (unit step): g at the new lambda is the
-    // residual of the solve plus H(l + d) - H(l), and |h'(t)| <= |t| e^|t|
-    // bounds that change by (tmax + tb_d) e^(tmax + tb_d) tb_d S_k (tb_d bounds
-    // |d.phi| on the grid); g itself carries at most err_k (the budget above,
-    // its x' term widened to the new lambda), and S_k at the new f is at least
-    // S_k (1 - tmax - tb_d).  The pointwise check moves by at most
-    // x'max e^tmax (e^tb_d - 1).  When both bounds hold, the step is taken
-    // and the histogram converged without the pass at the new lambda.
-    if (did_pass && step == 1.f && !viol && !unc) {
-      float dd[4];
+    // Newton correction from the Jacobian of H that the pass measured:
+    // g(l + d) = g(l) - M d + J d + R2 with J = sum vol phi phi^T x' h'(t), so
+    // d3 = M^-1 (J (d1 + d2)) makes d1 + d2 + d3 solve (M - J) d = g up to
+    // terms of second order (|J| is of order |t| |M|).  Without a pass,
+    // lambda = 0 and J = 0.
+    float dd[4], d3[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int k = 0; k < 4; ++k) dd[k] = d1[k] + d2[k];
-      const float tbd = fabsf(dd[0]) + fabsf(dd[1]) * fg.vmax + fabsf(dd[2]) * fg.wmax +
-                        fabsf(dd[3]) * fg.vmax * fg.vmax;
+    for (int k = 0; k < 4; ++k) dd[k] = d1[k] + d2[k];
+    float vk = 0.f;  // (J dd)_k in lane k
+    if (did_pass) {
+      vk = fmaf(Jr[3], dd[3], fmaf(Jr[2], dd[2], fmaf(Jr[1], dd[1], Jr[0] * dd[0])));
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r[k] = __shfl_sync(FULL, vk, k);
+      chol_solve(ch, r, d3);
+    }
+    // Certificate after a pass (unit step d = d1 + d2 + d3): in row k,
+    //   g_k(l + d) = (g - M dd)_k + (J dd - M d3 + J d3)_k + e_J + R2_k,
+    // the first term in double-float, the second in FP32 (roundings within
+    // 1e-6 of the sum of the magnitudes of its products, which also covers
+    // dd's rounding of d1 + d2); e_J, the FP32 error of J, is below
+    // 1e-5 tmax e^tmax tb_d S_k (|h'(t)| <= |t| e^|t|, about 70 roundings
+    // per sum; tb_d bounds |d.phi| on the grid); the remainder of the
+    // expansion is |R2_k| <= e^tt tb_d^2 S_k / 2 (h'' = e^-t, tt = tmax + tb_d).
+    // g itself carries at most err_k (the budget above, its x' term widened
+    // to the new lambda), and S_k at the new f is at least S_k (1 - tt).  The
+    // pointwise check moves by at most x'max e^tmax (e^tb_d - 1).  When both
+    // bounds hold, the step is taken and the histogram converged without the
+    // pass at the new lambda.
+    if (did_pass && step == 1.f && !viol && !unc) {
+      float dn[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) dn[k] = dd[k] + d3[k];
+      const float tbd = (fabsf(dn[0]) + fabsf(dn[1]) * fg.vmax + fabsf(dn[2]) * fg.wmax +
+                         fabsf(dn[3]) * fg.vmax * fg.vmax) *
+                        1.000001f;
       const float tt = tmax + tbd;
       if (tt < 0.05f) {
         const float grow = (1.f + 1.1f * tt) * 1.01f;  // e^tt for tt < 0.05, padded
-        // residual of the solve, row k in lane k: g - M (d1 + d2)
+        // residual of the solve, row k in lane k: g - M dd
         df md = df_mul_f(rowM[0], dd[0]);
 #pragma unroll
         for (int l = 1; l < 4; ++l) md = df_add(md, df_mul_f(rowM[l], dd[l]));
         const df gl = kr == 0 ? gk[0] : (kr == 1 ? gk[1] : (kr == 2 ? gk[2] : gk[3]));
         const float Sk = kr == 0 ? mo.S[0] : (kr == 1 ? mo.S[1] : (kr == 2 ? mo.S[2] : mo.S[3]));
+        const float rs = df_add(gl, df_neg(md)).hi;
+        float corr = vk, cabs = fabsf(rs);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          corr = fmaf(Jr[l] - rowM[l].hi, d3[l], corr);
+          cabs = fmaf(fabsf(Jr[l]) + fabsf(rowM[l].hi), fabsf(dd[l]) + fabsf(d3[l]), cabs);
+        }
         const float ek = erel * Sk +
                          3.7e-12f * c.dl_f * tbd *
-                             (kr == 0 ? fg.wk[0] : (kr == 1 ? fg.wk[1] : (kr == 2 ? fg.wk[2] : fg.wk[3])));
-        const float bk = fabsf(df_add(gl, df_neg(md)).hi) + ek + Sk * (tt * grow * tbd);
+                             (kr == 0 ? fg.wk[0] : (kr == 1 ? fg.wk[1] : (kr == 2 ? fg.wk[2] : fg.wk[3]))) +
+                         1e-6f * cabs + Sk * grow * tbd * fmaf(1e-5f, tmax, 0.5f * tbd);
+        const float bk = fabsf(rs + corr) + ek;
         const float rel = bk *
                           (kr == 0 ? invS[0] : (kr == 1 ? invS[1] : (kr == 2 ? invS[2] : invS[3]))) *
                           fmaf(1.06f, tt, 1.f);
@@ -916,6 +1005,7 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
           for (int k = 0; k < 4; ++k) {
             lam[k] = df_add_f(lam[k], d1[k]);
             lam[k] = df_add_f(lam[k], d2[k]);
+            lam[k] = df_add_f(lam[k], d3[k]);
             ns.gres[k] = __shfl_sync(FULL, rel, k);
           }
           *iters = it + 1;
@@ -929,6 +1019,7 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
     for (int k = 0; k < 4; ++k) {
       lam[k] = df_add_f(lam[k], step * d1[k]);
       lam[k] = df_add_f(lam[k], step * d2[k]);
+      lam[k] = df_add_f(lam[k], step * d3[k]);
     }
   }
 }
@@ -1293,6 +1384,8 @@ int make_fast_grid(const GridK& g, FastGridK* out) {
       const double cf = r <= p ? binom[p][r] * pow(b, r) * pow(c0, p - r) : 0.0;
       split_df(cf, &f.coef_h[p][r], &f.coef_l[p][r]);
     }
+  f.b_f = (float)b;
+  f.c0_f = (float)c0;
   f.vmax = (float)vmax;
   f.wmax = (float)g.vperp2[g.n_perp - 1];
   {

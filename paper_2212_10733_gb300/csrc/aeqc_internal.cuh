@@ -56,6 +56,12 @@ struct ParamsK {
   // float copies for the fast kernel (no per-histogram conversions)
   double alpha4;  // alpha / 4 (the retry level)
   float tau_f, step_f, tol_f, warm_reject_f, qoi_check_f;
+  // bin width on the integer pipe (fast kernel): set when tau is a normal
+  // double and 2 alpha and 2 alpha / 4 are powers of two, 2^a2_e[level];
+  // tau = tau_m 2^(tau_e - 52) with tau_m in [2^52, 2^53)
+  int bw_int;
+  int tau_e, a2_e[2];
+  unsigned long long tau_m;
 };
 
 // Build kernel blocks from the public structs (validates; returns AEQC_*).

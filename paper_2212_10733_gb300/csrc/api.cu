@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cfloat>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -99,6 +100,17 @@ int make_params(const aeqc_params* p, ParamsK* k) {
   k->loss = p->loss;
   k->warm_iters = p->warm_iters;
   k->alpha4 = p->alpha * 0.25;
+  {
+    // exact powers of two 2 alpha = 2^e (frexp gives mantissa 0.5 exactly)
+    int e2 = 0, e24 = 0, et = 0;
+    const double m2 = std::frexp(2.0 * p->alpha, &e2), m24 = std::frexp(2.0 * k->alpha4, &e24);
+    const double mt = std::frexp(p->tau, &et);
+    k->bw_int = m2 == 0.5 && m24 == 0.5 && p->tau >= DBL_MIN && 2.0 * k->alpha4 >= DBL_MIN;
+    k->a2_e[0] = e2 - 1;
+    k->a2_e[1] = e24 - 1;
+    k->tau_e = et - 1;  // tau in [2^tau_e, 2^(tau_e + 1))
+    k->tau_m = (unsigned long long)std::ldexp(mt, 53);  // exact: 53-bit significand
+  }
   k->tau_f = (float)p->tau;
   k->step_f = (float)p->step_s;
   k->tol_f = (float)p->tol;

@@ -112,13 +112,51 @@ __device__ __forceinline__ df df_from_ll(long long v) {
   const int lz = __clzll((long long)a);
   const unsigned long long m = a << lz;
   const int e = 63 - lz;
-  float hi = __fmul_rn(__uint2float_rn((unsigned)(m >> 40)), exp2i(e - 23));
-  float lo = __fmul_rn(__uint2float_rn((unsigned)((m >> 16) & 0xFFFFFFull)), exp2i(e - 47));
+  // top 24 bits (leading bit set) straight into a float's fields; the next
+  // 24 as two exact 12-bit halves (int->float conversion instructions issue
+  // to the FP64 pipe on this GPU)
+  float hi = __int_as_float(((e + 127) << 23) | (int)((m >> 40) & 0x7FFFFFull));
+  const unsigned l24 = (unsigned)((m >> 16) & 0xFFFFFFull);
+  const float l24f = fmaf(__int_as_float(0x4B000000 | (int)(l24 >> 12)) - 8388608.f, 4096.f,
+                          __int_as_float(0x4B000000 | (int)(l24 & 0xFFFu)) - 8388608.f);
+  float lo = __fmul_rn(l24f, exp2i(e - 47));
   if (v < 0) {
     hi = -hi;
     lo = -lo;
   }
   return quick_sum(hi, lo);
+}
+
+// hi + lo as a double on the integer pipe, for a pair with |lo| <= ulp(hi)
+// (as quick_sum leaves it): hi's 24-bit significand widened to 53 bits plus
+// lo aligned to it, lo's bits below the 53 truncated (the result is within one
+// unit in the last place of hi + lo).  A zero, subnormal or non-finite hi takes
+// the FP64 conversion.
+__device__ __forceinline__ double df_to_double(df x) {
+  const unsigned uh = __float_as_uint(x.hi), ul = __float_as_uint(x.lo);
+  const int eh = (int)((uh >> 23) & 0xffu), el = (int)((ul >> 23) & 0xffu);
+  if (eh == 0 || eh == 255) return (double)x.hi + (double)x.lo;
+  // hi = S 2^(eh - 179) with S in [2^52, 2^53)
+  long long S = (long long)((uh & 0x7fffffu) | 0x800000u) << 29;
+  int e = eh;
+  if (el != 0) {
+    // lo = L 2^(el - 150) = L 2^(el - eh + 29) units of hi's last place
+    const long long L = (long long)((ul & 0x7fffffu) | 0x800000u);
+    const int sh = eh - el - 29;  // >= -5 for |lo| <= ulp(hi)
+    const long long Ls = sh <= 0 ? (L << (-sh)) : (sh < 63 ? (L >> sh) : 0ll);
+    S += ((uh ^ ul) >> 31) ? -Ls : Ls;
+    if (S >= (1ll << 53)) {
+      S >>= 1;
+      ++e;
+    } else if (S < (1ll << 52)) {
+      S <<= 1;
+      --e;
+    }
+  }
+  const unsigned long long bits = ((unsigned long long)(uh >> 31) << 63) |
+                                  ((unsigned long long)(e + 896) << 52) |
+                                  ((unsigned long long)S & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
 }
 
 // ---- integer decomposition of the inputs ----------------------------------
@@ -144,10 +182,38 @@ struct QConst {
   int thr;   // exponent field of xhat at or above which |q| > 32766 for sure
 };
 
-__device__ __forceinline__ bool make_qconst(double tau, double s, double alpha, QConst& c) {
-  c.dl = bin_width(tau, s, alpha);
-  if (!(c.dl > 0.0) || !isfinite(c.dl)) return false;
-  c.k = exponent_of(c.dl) - 1;
+// floor(log2(2 alpha fl(tau s))) for 2 alpha = 2^a2e and tau, s > 0 normal, on
+// the integer pipe (the FP64 pipe issues one warp instruction in ~60 cycles
+// on this GPU): fl(tau s) = 2^(et + es + top + carry) (1 + f) with top set
+// when the significand product P = mt ms (in [2^104, 2^106)) reaches 2^105,
+// and carry when rounding P to 53 bits, to nearest even, overflows into the
+// next binade; scaling by 2^a2e is exact.  Results outside the normal range
+// are rejected by the caller, as the FP64 form of bin_width would be.
+__device__ __forceinline__ int bin_exp_int(unsigned long long mt, int et, unsigned long long us,
+                                           int a2e) {
+  const unsigned long long ms = (us & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int es = (int)(us >> 52) - 1023;
+  const unsigned long long lo = mt * ms, hi = __umul64hi(mt, ms);
+  const int top = (int)(hi >> 41);
+  const unsigned long long sig = top ? ((hi << 11) | (lo >> 53)) : ((hi << 12) | (lo >> 52));
+  const unsigned long long rb = top ? (lo >> 52) & 1ull : (lo >> 51) & 1ull;
+  // sig = 2^53 - 1 is odd: a set round bit rounds it up (to even) whatever
+  // the sticky bits
+  const int carry = (rb && sig == (1ull << 53) - 1ull) ? 1 : 0;
+  return et + es + top + carry + a2e;
+}
+
+__device__ __forceinline__ bool make_qconst(const ParamsK& pr, double s, int level, QConst& c) {
+  const unsigned long long us = (unsigned long long)__double_as_longlong(s);
+  if (pr.bw_int && (us >> 52) != 0) {  // s > 0 and normal
+    c.k = bin_exp_int(pr.tau_m, pr.tau_e, us, pr.a2_e[level]);
+    if (c.k < -1022 || c.k > 1023) return false;
+    c.dl = __longlong_as_double((long long)(c.k + 1023) << 52);
+  } else {
+    c.dl = bin_width(pr.tau, s, level ? pr.alpha4 : pr.alpha);
+    if (!(c.dl > 0.0) || !isfinite(c.dl)) return false;
+    c.k = exponent_of(c.dl) - 1;
+  }
   const int IBx = exponent_of(s) - c.k;  // s / Delta < 2^IBx
   c.cx = 1085 + c.k - QF;
   c.ch = 190 + c.k - QF;
@@ -1168,7 +1234,7 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
 #pragma unroll 1
   for (int level = 0; level < 2 && !defer && !done; ++level) {
     QConst c;
-    if (!make_qconst(pr.tau, s, level ? pr.alpha4 : pr.alpha, c)) {
+    if (!make_qconst(pr, s, level, c)) {
       defer = true;
       break;
     }
@@ -1271,7 +1337,7 @@ __device__ void fast_histogram(const FusedArgs& a, FastWS& w, long long b, int l
   {
     const int k = lane & 3;
     const df lk = k == 0 ? lam[0] : (k == 1 ? lam[1] : (k == 2 ? lam[2] : lam[3]));
-    lamd = (double)lk.hi + (double)lk.lo;
+    lamd = df_to_double(lk);
   }
   // outputs (the codes are in place)
   if (a.f_out) {

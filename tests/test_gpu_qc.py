@@ -455,3 +455,51 @@ def test_verbatim_after_the_retry_matches_oracle(aq, grids, kernel):
     assert np.all(out.lam.cpu().numpy()[vb] == 0.0)
     assert np.array_equal(out.f.cpu().numpy()[vb], x[vb])
     assert np.all(out.codes.cpu().numpy()[vb] == oracle.ESCAPE)
+
+
+def carry_maxima(tau, count):
+    """Row maxima s at which fl(tau s) lands exactly on a power of two although
+    tau s is below it (the rounding carries into the next binade: Delta doubles
+    there), each paired with the largest s whose product stays below."""
+    from fractions import Fraction
+    import math
+    carry, below = [], []
+    for m in range(-10, 30):
+        t = math.ldexp(1.0, m) / tau
+        s = t
+        for _ in range(8):
+            if tau * s == math.ldexp(1.0, m) and Fraction(tau) * Fraction(s) < Fraction(2) ** m:
+                carry.append(s)
+            elif tau * s < math.ldexp(1.0, m):
+                below.append(s)
+                break
+            s = math.nextafter(s, 0.0)
+        if len(carry) >= count:
+            break
+    return carry[:count], below[:count]
+
+
+# (whether such maxima exist depends on tau's significand alone: for 1e-4
+# they do not, for 1.1e-4 and 3e-3 at every power of two)
+@pytest.mark.parametrize("tau", [1.1e-4, 3e-3])
+def test_bin_width_at_binade_carries_matches_oracle(aq, grids, tau):
+    """The fast kernel takes the bin width's exponent from the integer
+    significand product of tau and max(x) (Sec. III Stage 4: Delta =
+    2^floor(log2(2 alpha tau max x)) with the products rounded in float64).
+    Rows whose maximum makes fl(tau s) round up onto a power of two, and rows
+    just below such a boundary, must get the oracle's Delta, codes, scale and
+    status."""
+    _, og = grids
+    carry, below = carry_maxima(tau, 16)
+    assert len(carry) >= 8
+    svals = np.array(carry + below)
+    x = synth.histograms(len(svals), synth.config_seed(0) + 71)
+    for r, s in enumerate(svals):
+        k = int(np.argmax(x[r]))
+        x[r] *= (s / x[r, k]) * (1.0 - 1e-9)
+        x[r, k] = s
+    assert np.array_equal(x.max(axis=1), svals)
+    xh = synth.stand_in_xhat(x, 72)
+    check_batch(aq, og, x, xh, tau, aq.KERNEL_FAST, n_expect_conv=0.9)
+    dl = np.array([oracle.delta(tau * s, 0.5) for s in svals])
+    assert len(np.unique(np.log2(dl[:len(carry)]))) > 1  # several binades

@@ -64,13 +64,14 @@ __device__ __forceinline__ uint32_t bf16_of_f64_words(uint32_t hi, uint32_t lo) 
   const uint32_t sign = (hi >> 16) & 0x8000u;
   const uint32_t a = (hi & 0x7FFFFFFFu) | (lo != 0u ? 1u : 0u);
   const uint32_t r = a + 0xFFFu + ((a >> 13) & 1u);
-  const uint32_t E = r >> 20;
-  const uint32_t v = sign | ((r >> 13) - (896u << 7));
-  // outside the BF16 normal range (zero, underflow, overflow, NaN): selects,
-  // not branches, since the zero row of every histogram makes lanes diverge
-  const uint32_t big = sign | (a > 0x7FF00000u ? 0x7FC0u : 0x7F80u);  // NaN / infinity
-  const uint32_t out = E <= 896u ? sign : big;
-  return E - 897u >= 254u ? out : v;
+  // the rounded magnitude with the exponent rebased to BF16's: below 128 the
+  // value is under the BF16 normal range (flushed to zero), from 0x7F80 up it
+  // overflows to infinity; a NaN input (a above infinity's pattern) gives
+  // the quiet NaN.  Clamps and selects, not branches, since the zero row of
+  // every histogram makes lanes diverge.
+  const int t = (int)(r >> 13) - (896 << 7);
+  const uint32_t m = t < 128 ? 0u : (uint32_t)min(t, 0x7F80);
+  return sign | (a > 0x7FF00000u ? 0x7FC0u : m);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {

@@ -292,7 +292,10 @@ __global__ void __launch_bounds__(ENC_NTHREADS, 1)
     // ---- converters / epilogue: sixteen warps, ENC_RPW rows each ----
     const int q = warp & 3, part = warp >> 2;
     const int r = q * 32 + lane;
-    int it = 0, iter = 0;
+    // stage and phase of the ring position, advanced by one per K block
+    // (no division by the runtime stage count on the converters' path)
+    int s_ring = 0, iter = 0;
+    uint32_t ph_ring = 0;
     bool ok = true;
     for (long long t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
       TileInfo ti;
@@ -306,9 +309,13 @@ __global__ void __launch_bounds__(ENC_NTHREADS, 1)
       long long mraw[ENC_RPW];
 #pragma unroll
       for (int i = 0; i < ENC_RPW; ++i) mraw[i] = (long long)0x8000000000000000ull;
-      for (int kb = 0; kb < nkb; ++kb, ++it) {
-        const int s = it % ns;
-        const uint32_t ph = (it / ns) & 1;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = s_ring;
+        const uint32_t ph = ph_ring;
+        if (++s_ring == ns) {
+          s_ring = 0;
+          ph_ring ^= 1u;
+        }
         if (*abort_flag || !mbar_wait(&empty[s], ph ^ 1)) {
           ok = false;
           break;

@@ -993,12 +993,14 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
       for (int k = 0; k < 4; ++k) lam[k] = df{step * d1[k], 0.f};
       continue;
     }
+    df rd1;  // g - M d1 in row kr (double-float), reused by the certificate
     {
       df md = df_mul_f(rowM[0], d1[0]);
 #pragma unroll
       for (int l = 1; l < 4; ++l) md = df_add(md, df_mul_f(rowM[l], d1[l]));
       const df gl = kr == 0 ? gk[0] : (kr == 1 ? gk[1] : (kr == 2 ? gk[2] : gk[3]));
-      const float rl = df_add(gl, df_neg(md)).hi;
+      rd1 = df_add(gl, df_neg(md));
+      const float rl = rd1.hi;
 #pragma unroll
       for (int k = 0; k < 4; ++k) r[k] = __shfl_sync(FULL, rl, k);
     }
@@ -1041,19 +1043,18 @@ __device__ int round1_fast(const GridK& g, const FastGridK& fg, const FastWS& w,
       const float tt = tmax + tbd;
       if (tt < 0.05f) {
         const float grow = (1.f + 1.1f * tt) * 1.01f;  // e^tt for tt < 0.05, padded
-        // residual of the solve, row k in lane k: g - M dd
-        df md = df_mul_f(rowM[0], dd[0]);
-#pragma unroll
-        for (int l = 1; l < 4; ++l) md = df_add(md, df_mul_f(rowM[l], dd[l]));
-        const df gl = kr == 0 ? gk[0] : (kr == 1 ? gk[1] : (kr == 2 ? gk[2] : gk[3]));
+        // residual of the solve, row k in lane k: g - M dd = (g - M d1) - M d2,
+        // the second product in FP32 (|d2| ~ 1e-6 |d1|; its rounding in cabs)
         const float Sk = kr == 0 ? mo.S[0] : (kr == 1 ? mo.S[1] : (kr == 2 ? mo.S[2] : mo.S[3]));
-        const float rs = df_add(gl, df_neg(md)).hi;
-        float corr = vk, cabs = fabsf(rs);
+        float rs = rd1.hi, corr = vk + rd1.lo, cabs = 0.f;
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
+          rs = fmaf(-rowM[l].hi, d2[l], rs);
           corr = fmaf(Jr[l] - rowM[l].hi, d3[l], corr);
-          cabs = fmaf(fabsf(Jr[l]) + fabsf(rowM[l].hi), fabsf(dd[l]) + fabsf(d3[l]), cabs);
+          cabs = fmaf(fabsf(Jr[l]) + fabsf(rowM[l].hi),
+                      fabsf(dd[l]) + fabsf(d2[l]) + fabsf(d3[l]), cabs);
         }
+        cabs += fabsf(rs);
         const float ek = erel * Sk +
                          3.7e-12f * c.dl_f * tbd *
                              (kr == 0 ? fg.wk[0] : (kr == 1 ? fg.wk[1] : (kr == 2 ? fg.wk[2] : fg.wk[3]))) +
